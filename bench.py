@@ -1,0 +1,361 @@
+"""Benchmark: MFLUP/s of the sparse D3Q19 TRT sweep on one GB300.
+
+Workload: the 1024x256x256 packed bed (tube of diameter 250 along x,
+spheres of radius 8 by seeded random sequential addition, periodic in x,
+~33 M fluid cells), body force 1e-6 along x, omega+ = 1/0.8, Lambda = 3/16,
+rest initial state, FP64 PDFs, 8^3-blocked lexicographic order.
+
+One "step" is one time step of the hot path: pull through the adjacency
+list, TRT collision, streaming store (one kernel launch per step), with the
+FP64 mass/flux reduction fused into the last step and finished by
+lbm_reduce_flux.  MFLUP/s counts fluid cells only (Sec. 7).
+
+The JSON line carries: value (device-resident inputs), e2e (the same metric
+through the C ABI from host flags to a host result, copies included),
+roofline of the sweep kernel, the CPU oracle timed on a bounded sample, the
+SM clocks sampled during the timed region, and extra measurements
+(orderings, storage forms) each labelled with its own step count.
+
+--impl reference times the CPU oracle instead (the only reference this
+method has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WP = 1.0 / 0.8
+FORCE = (1e-6, 0.0, 0.0)
+AXIS = 0
+BYTES_PER_LUP = {"f64": 19 * 8 * 2 + 18 * 4, "f32": 19 * 4 * 2 + 18 * 4,
+                 "f32s": 19 * 4 * 2 + 18 * 4, "f16s": 19 * 2 * 2 + 18 * 4,
+                 "bf16s": 19 * 2 * 2 + 18 * 4}
+WORKLOADS = {
+    "large": ("packed bed 1024x256x256, tube D=250 along x, spheres r=8, seed 0", "bed_large"),
+    "medium": ("packed bed 256x128x128, tube D=122 along x, spheres r=8, seed 0", "bed_medium"),
+}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _oracle_sample(bed, budget_s: float, max_steps: int | None = None):
+    """The CPU oracle on a bounded slab of the bed (x in [0, 64), periodic
+    in x): returns (MFLUP/s, steps, fluid cells, cores, seconds)."""
+    import numpy as np
+
+    import oracle
+
+    slab = np.ascontiguousarray(bed.flags[:, :, :64])
+    n_fluid = int((slab == 0).sum())
+    wm = oracle.omega_minus(WP)
+    f = oracle.rest_state(slab)
+    t0 = time.perf_counter()
+    f, _, _, _ = oracle.run(slab, 1, WP, wm, FORCE, 1, f=f)
+    one = time.perf_counter() - t0
+    steps = max(1, int(budget_s / max(one, 1e-6)))
+    if max_steps is not None:
+        steps = min(steps, max_steps)
+    t0 = time.perf_counter()
+    oracle.run(slab, 1, WP, wm, FORCE, steps, f=f)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return n_fluid * steps / dt / 1e6, steps, n_fluid, cores, dt
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1111_1129_gb300 import inputs
+    bed = getattr(inputs, WORKLOADS[args.workload][1])(0)
+    for _ in range(args.warmup):
+        _oracle_sample(bed, 0.5, max_steps=1)
+    t0 = time.perf_counter()
+    lups = 0.0
+    samples = []
+    for _ in range(args.steps):
+        mflups, steps, n_fluid, cores, dt = _oracle_sample(bed, 3.0)
+        lups += n_fluid * steps
+        samples.append(steps)
+    dt = time.perf_counter() - t0
+    value = lups / dt / 1e6
+    line = {
+        "impl": "reference", "metric": "MFLUP/s", "value": value, "unit": "MFLUP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload][0], "ordering": "dense full-array oracle",
+                   "precision": "f64", "cells_per_step": None},
+        "cpu_baseline": {"value": value, "unit": "MFLUP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"each step: 64x256x256 slab of the bed (x in [0,64), "
+                                   f"periodic x, {n_fluid} fluid cells), ~3 s of oracle "
+                                   f"time steps ({samples[0]} steps in the first)"},
+        "e2e": {"value": value, "unit": "MFLUP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1111_1129_gb300 import LBMState, SparseLattice, capi, inputs, omega_minus
+    from paper_1111_1129_gb300 import lbm as lbm_mod
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    capi.load()
+    wm = omega_minus(WP)
+    # weak scaling: each rank owns an independent bed (seed = rank)
+    bed = getattr(inputs, WORKLOADS[args.workload][1])(rank)
+    flags_host = torch.from_numpy(bed.flags).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    lat = SparseLattice(flags_host.cuda(), args.ordering, (8, 8, 8), bed.periodic)
+    n = lat.n
+    st = LBMState(lat, args.precision)
+    st.step(args.warmup, WP, wm, FORCE)
+    st.reduce_flux(AXIS)
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        ev0.record(stream)
+        st.step(args.steps, WP, wm, FORCE)
+        mass, flux = st.reduce_flux(AXIS)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        tot = torch.tensor([float(n)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tot)
+        total_cells = float(tot.item())
+    else:
+        total_cells = float(n)
+    value = total_cells * args.steps / (ms * 1e-3) / 1e6
+    launch_ms = ms / args.steps
+    st.close()
+
+    # ---- e2e: host flags -> C ABI -> host result, copies inside ----------
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    flags_dev = flags_host.to("cuda", non_blocking=True)
+    h_lat = capi.lbm_build_sparse(flags_dev.data_ptr(), bed.dims,
+                                  capi.make_ordering(lbm_mod.ORDERINGS[args.ordering],
+                                                     (8, 8, 8), bed.periodic),
+                                  int(stream.cuda_stream))
+    h_st = capi.lbm_state_create(h_lat, lbm_mod.PRECISIONS[args.precision], 0)
+    capi.lbm_step(h_st, args.steps, WP, wm, FORCE)
+    e2e_mass, e2e_flux = capi.lbm_reduce_flux(h_st, AXIS)
+    e2e_s = time.perf_counter() - t0
+    capi.lbm_free(h_st)
+    capi.lbm_free(h_lat)
+    e2e_value = n * args.steps / e2e_s / 1e6
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_value = total_cells * args.steps / float(t.item()) / 1e6
+
+    extra = {}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_extra:
+        extra = _extras(lat, bed, wm, args)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        mflups, steps_c, n_c, cores, dt = _oracle_sample(bed, args.cpu_seconds)
+        cpu = {"value": mflups, "unit": "MFLUP/s", "cores": cores, "kind": "oracle",
+               "sample": f"64x256x256 slab of the bed (x in [0,64), periodic x, {n_c} fluid "
+                         f"cells), {steps_c} FP64 steps of the dense full-array oracle "
+                         f"({dt:.1f} s)"}
+    lat.close()
+    peak, peak_kind = _peaks()
+    bpl = BYTES_PER_LUP[args.precision]
+    achieved = bpl * n / (launch_ms * 1e-3) / 1e9
+    line = {
+        "metric": "MFLUP/s", "value": value, "unit": "MFLUP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload][0], "fluid_cells_per_gpu": n, "ordering": f"{args.ordering}"
+                   + (" 8^3" if args.ordering == "blocked" else ""),
+                   "precision": args.precision, "force": list(FORCE),
+                   "omega_plus": WP, "omega_minus": wm,
+                   "l2": "inputs larger than L2 (PDFs+adjacency ~%.1f GB)" % (
+                       (2 * 19 * (bpl - 72) / 38 + 72) * n / 1e9),
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "bytes_per_lup": bpl, "peak_kind": peak_kind,
+                     "kernel": f"sweep_kernel<{args.precision}>"},
+        "e2e": {"value": e2e_value, "unit": "MFLUP/s",
+                "h2d_bytes_per_step": (bed.flags.nbytes + 24) / args.steps,
+                "d2h_bytes_per_step": 32 / args.steps},
+        "gpu_launches": args.steps + 1,
+        "clocks": clocks.summary(),
+        "result": {"mass": mass, "flux": flux, "e2e_flux": e2e_flux},
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if extra:
+        line["extra"] = extra
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def _extras(lat, bed, wm, args):
+    """Short labelled runs: the other orderings (FP64) and the other storage
+    forms (8^3 blocked)."""
+    import torch
+
+    from paper_1111_1129_gb300 import LBMState, SparseLattice
+
+    def timed(lattice, precision, steps, scale_exp=0):
+        st = LBMState(lattice, precision, scale_exp)
+        st.step(3, WP, wm, FORCE)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st.step(steps, WP, wm, FORCE)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st.close()
+        return lattice.n * steps / (ms * 1e-3) / 1e6
+
+    out = {"steps_each": args.extra_steps}
+    orders = {}
+    for name in ("lex", "blocked", "morton1", "morton2"):
+        if name == args.ordering:
+            l2 = lat
+        else:
+            l2 = SparseLattice(torch.from_numpy(bed.flags).cuda(), name, (8, 8, 8), bed.periodic)
+        orders[name + (" 8^3" if name == "blocked" else "")] = timed(l2, "f64", args.extra_steps)
+        if l2 is not lat:
+            l2.close()
+    out["f64_by_ordering_mflups"] = orders
+    forms = {}
+    for prec, k in (("f32", 0), ("f32s", 0), ("f16s", 24), ("bf16s", 24)):
+        forms[prec] = timed(lat, prec, args.extra_steps, k)
+    out["by_storage_mflups"] = forms
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=list(WORKLOADS))
+    ap.add_argument("--ordering", default="blocked", choices=["lex", "blocked", "morton1",
+                                                               "morton2"])
+    ap.add_argument("--precision", default="f64", choices=list(BYTES_PER_LUP))
+    ap.add_argument("--extra-steps", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,214 @@
+/*
+ * lbm.h -- C ABI of the GB300 sparse D3Q19 TRT lattice Boltzmann library.
+ *
+ * The library implements the hot path of a list-based lattice Boltzmann flow
+ * solver (Wittmann, Zeiser, Hager, Wellein, "Domain decomposition and
+ * locality optimization for large-scale lattice Boltzmann simulations"):
+ *
+ *   - assembly of the sparse representation of a voxelised domain: only
+ *     fluid cells are stored, in a 1-D array ordered by a numbering scheme,
+ *     with an adjacency list in which bounce back is implicit (Sec. 2,
+ *     "sparse representation"; Sec. 3, "Numbering scheme" and the contiguous
+ *     index I_c in [1, N_f]);
+ *   - the D3Q19 two-relaxation-time (TRT) stream-collide sweep over that
+ *     list, pull scheme, structure-of-arrays PDFs (Sec. 1; Sec. 7, first
+ *     paragraph), with FP64 mass and flux reductions.
+ *
+ * Conventions (the paper names D3Q19 and TRT but prints neither):
+ *   - dims = {nx, ny, nz}; box cell (x, y, z) has linear index
+ *     x + nx*(y + ny*z); flags[] uses that layout, 0 = fluid, 1 = solid.
+ *   - velocities: q = 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = face
+ *     diagonals (+1,+1,0),(-1,-1,0),(+1,-1,0),(-1,+1,0),(+1,0,+1),(-1,0,-1),
+ *     (+1,0,-1),(-1,0,+1),(0,+1,+1),(0,-1,-1),(0,+1,-1),(0,-1,+1);
+ *     opp(q) = q+1 for odd q, q-1 for even q > 0.  Weights 1/3, 1/18, 1/36.
+ *   - sparse index n = I_c - 1 (0-based) of the paper's contiguous index.
+ *   - PDFs are structure of arrays: f[q*N + n].
+ *   - adjacency adj[(i-1)*N + n], i = 1..18, is the flat source slot of the
+ *     pull for direction i: i*N + m when the upwind cell x - c_i is the fluid
+ *     cell m, else opp(i)*N + n (half-way bounce back, applied implicitly;
+ *     Sec. 2).  The rest direction has no entry (it is always slot n).
+ *   - TRT collision with body force F and Brinkman damping alpha (rho0 = 1):
+ *       rho = sum g,  j = sum c g,  u = (j + F/2) / (1 + alpha/2),
+ *       F_n = F - alpha u,
+ *       e_q = w_q (rho + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u),
+ *       f*_q = g_q - w+ (g+ - e+)_q - w- (g- - e-)_q + (1 - w-/2) 3 w_q c_q.F_n.
+ *
+ * Every function returns LBM_OK (0) or a negative status; lbm_last_error()
+ * then returns a description (thread-local, valid until the next call from
+ * the same thread).  No C++ exception crosses this interface.
+ *
+ * Device pointers are plain CUDA device addresses on the current device.
+ * Handles (lbm_sparse, lbm_state) own device memory; they are released by
+ * lbm_free.  A state refers to the sparse representation it was created
+ * from, which must outlive it.  All work is queued on the stream given to
+ * lbm_build_sparse (a cudaStream_t passed as void*, NULL = legacy default
+ * stream); functions that return host values synchronise that stream.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)      /* bad argument (null pointer, size, range) */
+#define LBM_EOVERFLOW (-2)   /* index space beyond int32: box >= 2^31 cells
+                                or 19*N >= 2^31 PDF slots */
+#define LBM_ECUDA (-3)       /* a CUDA runtime call failed */
+#define LBM_ENONFINITE (-4)  /* a reduction produced NaN or Inf */
+#define LBM_ETIMEOUT (-5)    /* queued work did not finish in the time limit */
+#define LBM_ENOMEM (-6)      /* device or pinned host allocation failed */
+#define LBM_EFLAGS (-7)      /* a flag byte other than 0 or 1 */
+
+/* ---- numbering schemes (Sec. 3, "Numbering scheme"; Sec. 7) ------------- */
+#define LBM_ORDER_LEX 0      /* lexicographic, x fastest */
+#define LBM_ORDER_BLOCKED 1  /* lexicographic with blocking: blocks of
+                                block[0] x block[1] x block[2] cells visited
+                                lexicographically, cells inside a block
+                                lexicographically, edge blocks clipped;
+                                block {1,1,1} equals LBM_ORDER_LEX */
+#define LBM_ORDER_MORTON1 2  /* Z curve, 1-bit interleave: key bit 3k = x_k,
+                                3k+1 = y_k, 3k+2 = z_k */
+#define LBM_ORDER_MORTON2 3  /* Z curve, 2-bit groups: key bits 6k..6k+1 =
+                                x bits 2k..2k+1, then y, then z */
+
+typedef struct lbm_ordering {
+  int32_t kind;      /* LBM_ORDER_* */
+  int32_t block[3];  /* blocking factors for LBM_ORDER_BLOCKED, each >= 1 */
+  uint32_t periodic; /* bit 0: x periodic, bit 1: y, bit 2: z; a closed
+                        face bounces PDFs back like a solid cell */
+} lbm_ordering;
+
+/* ---- storage precisions -------------------------------------------------- */
+#define LBM_F64 0   /* f in FP64, FP64 arithmetic (the paper's form, Sec. 7) */
+#define LBM_F32 1   /* f in FP32, FP32 arithmetic */
+#define LBM_F32S 2  /* f - w_q in FP32, FP32 arithmetic */
+#define LBM_F16S 3  /* (f - w_q) * 2^k in FP16, FP32 arithmetic */
+#define LBM_BF16S 4 /* (f - w_q) * 2^k in BF16, FP32 arithmetic */
+
+typedef struct lbm_sparse lbm_sparse;
+typedef struct lbm_state lbm_state;
+
+/*
+ * Numbering-scheme key I(x,y,z) of every box cell (Sec. 3, "Numbering
+ * scheme": a unique, not necessarily contiguous index of all cells).
+ * keys_dev: device uint64[nx*ny*nz] in box layout, written on `stream`.
+ * Returns LBM_EINVAL for bad dims or ordering.
+ */
+int lbm_ordering_keys(const int32_t dims[3], lbm_ordering ord, uint64_t* keys_dev,
+                      void* stream);
+
+/*
+ * Build the sparse representation of a voxelised domain (Sec. 2-3).
+ * flags_dev: device uint8[nx*ny*nz], box layout, 0 fluid / 1 solid, read
+ *            only, owned by the caller, must stay valid until this call
+ *            returns.
+ * dims:      host int32[3], each >= 1, nx*ny*nz < 2^31 (the paper's solver
+ *            has the same bound on the bounding box, Sec. 7 end).
+ * ord:       numbering scheme and periodic axes.
+ * stream:    cudaStream_t used by this handle and every state built on it.
+ * out:       receives a library-owned handle holding, in device memory,
+ *            cells[N] (box index of the fluid cell with I_c = n + 1, i.e.
+ *            fluid cells ranked by key), inv[nx*ny*nz] (n, or -1 for solid)
+ *            and adj[18*N] (layout above).
+ * The call synchronises `stream` (to learn N, and again before returning,
+ * so flags_dev may be released afterwards).  Errors: LBM_EINVAL,
+ * LBM_EFLAGS, LBM_EOVERFLOW (19*N >= 2^31), LBM_ENOMEM, LBM_ECUDA.
+ */
+int lbm_build_sparse(const uint8_t* flags_dev, const int32_t dims[3], lbm_ordering ord,
+                     void* stream, lbm_sparse** out);
+
+/*
+ * Read-only views of a sparse representation.  Any out pointer may be NULL.
+ * The device pointers stay owned by the handle.
+ */
+int lbm_sparse_info(const lbm_sparse* sp, int64_t* n_fluid, const int32_t** cells_dev,
+                    const int32_t** adj_dev, const int32_t** inv_dev);
+
+/*
+ * Create a solver state on a sparse representation: two PDF buffers (A/B,
+ * pull scheme with swapped grids, Sec. 7) initialised to rest,
+ * f_q = w_q (rho0 = 1).
+ * precision: LBM_F64 .. LBM_BF16S.
+ * scale_exp: k of the 16-bit shifted forms, stored value (f - w_q) * 2^k
+ *            rounded to nearest; 0 <= k <= 40; ignored by the other forms.
+ * Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA.
+ */
+int lbm_state_create(const lbm_sparse* sp, int32_t precision, int32_t scale_exp,
+                     lbm_state** out);
+
+/*
+ * Overwrite the current PDFs from device FP64 f_dev[19*N] (layout above),
+ * converting to the state's storage form; clears the step count.
+ * lbm_state_get_pdfs decodes the current PDFs into f_dev[19*N] as FP64.
+ * Both are queued on the state's stream.
+ */
+int lbm_state_set_pdfs(lbm_state* st, const double* f_dev);
+int lbm_state_get_pdfs(const lbm_state* st, double* f_dev);
+
+/*
+ * Per-cell Brinkman damping alpha_n >= 0 in fluid order (device FP64[N]),
+ * copied into the state in its arithmetic precision; NULL removes damping.
+ */
+int lbm_set_damping(lbm_state* st, const double* alpha_dev);
+
+/*
+ * Advance n_steps >= 0 time steps: each is a pull through the adjacency
+ * list, a TRT collision and a store to the other grid (Sec. 7: pull scheme,
+ * structure of arrays, streaming stores).  omega_plus / omega_minus are the
+ * even / odd relaxation rates, each in (0, 2); force is a host double[3]
+ * body force, finite.  The last step of the call also writes FP64 block
+ * partial sums of rho and u for lbm_reduce_flux.  Asynchronous on the
+ * state's stream.  Errors: LBM_EINVAL, LBM_ECUDA.
+ */
+int lbm_step(lbm_state* st, int32_t n_steps, double omega_plus, double omega_minus,
+             const double force[3]);
+
+/*
+ * Mass and mean axial velocity of the most recent step's collision:
+ * mass = sum_n rho_n and flux = (1/N) sum_n u_axis,n, both in FP64 with a
+ * fixed summation order (run to run identical).  axis in {0,1,2}.
+ * Synchronises the stream (bounded by lbm_set_timeout).  Errors:
+ * LBM_EINVAL (no step taken yet, bad axis), LBM_ENONFINITE, LBM_ETIMEOUT,
+ * LBM_ECUDA.
+ */
+int lbm_reduce_flux(lbm_state* st, int32_t axis, double* mass_out, double* flux_out);
+
+/*
+ * Per-cell rho_dev[N] and u_dev[3*N] (u_dev[k*N + n]) of the most recent
+ * step's collision, in FP64, recomputed from the previous grid with the
+ * same arithmetic as the step.  Errors: LBM_EINVAL if no step was taken.
+ */
+int lbm_moments(const lbm_state* st, double* rho_dev, double* u_dev);
+
+/* Number of steps taken since creation or the last lbm_state_set_pdfs. */
+int lbm_state_steps(const lbm_state* st, int64_t* steps);
+
+/*
+ * Wait for the state's queued work, polling with a wall-clock limit of
+ * timeout_s seconds (<= 0: the library default, 600 s).  Returns
+ * LBM_ETIMEOUT if the work is still running at the limit; the work itself
+ * is not cancelled.
+ */
+int lbm_synchronize(const lbm_state* st, double timeout_s);
+void lbm_set_timeout(double timeout_s);
+
+/* Release a handle returned by this library (sparse or state); NULL is a
+ * no-op.  Waits for the handle's stream before freeing. */
+void lbm_free(void* handle);
+
+/* Description of the last failure on this thread ("" if none). */
+const char* lbm_last_error(void);
+
+/* ABI version, currently 1. */
+int32_t lbm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

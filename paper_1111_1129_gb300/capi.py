@@ -1,0 +1,174 @@
+"""ctypes binding of the C ABI declared in ``include/lbm.h``.
+
+Argument marshalling only: every function here forwards to the function of
+the same name in ``liblbm_gb300.so`` and turns a negative status into
+:class:`LbmError`.  There is no fallback: if the library is missing or does
+not load, :func:`load` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+LBM_OK, LBM_EINVAL, LBM_EOVERFLOW, LBM_ECUDA = 0, -1, -2, -3
+LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ENOMEM, LBM_EFLAGS = -4, -5, -6, -7
+LBM_ORDER_LEX, LBM_ORDER_BLOCKED, LBM_ORDER_MORTON1, LBM_ORDER_MORTON2 = 0, 1, 2, 3
+LBM_F64, LBM_F32, LBM_F32S, LBM_F16S, LBM_BF16S = 0, 1, 2, 3, 4
+
+# Every exported entry point with (restype, argtypes); the symbol test checks
+# this list against the declarations in include/lbm.h.
+_vp, _i32, _i64, _u32, _d = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                             ctypes.c_double)
+
+
+class lbm_ordering(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("block", ctypes.c_int32 * 3),
+                ("periodic", ctypes.c_uint32)]
+
+
+SIGNATURES = {
+    "lbm_ordering_keys": (ctypes.c_int, [_vp, lbm_ordering, _vp, _vp]),
+    "lbm_build_sparse": (ctypes.c_int, [_vp, _vp, lbm_ordering, _vp, _vp]),
+    "lbm_sparse_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "lbm_state_create": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
+    "lbm_state_set_pdfs": (ctypes.c_int, [_vp, _vp]),
+    "lbm_state_get_pdfs": (ctypes.c_int, [_vp, _vp]),
+    "lbm_set_damping": (ctypes.c_int, [_vp, _vp]),
+    "lbm_step": (ctypes.c_int, [_vp, _i32, _d, _d, _vp]),
+    "lbm_reduce_flux": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
+    "lbm_moments": (ctypes.c_int, [_vp, _vp, _vp]),
+    "lbm_state_steps": (ctypes.c_int, [_vp, _vp]),
+    "lbm_synchronize": (ctypes.c_int, [_vp, _d]),
+    "lbm_set_timeout": (None, [_d]),
+    "lbm_free": (None, [_vp]),
+    "lbm_last_error": (ctypes.c_char_p, []),
+    "lbm_abi_version": (ctypes.c_int32, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"lbm status {status}: {message}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load ``liblbm_gb300.so``; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing: build it first "
+                                   "(python -c 'import __graft_entry__ as g; g.build()')")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != LBM_OK:
+        raise LbmError(status, load().lbm_last_error().decode(errors="replace"))
+
+
+def _dims(dims):
+    return (ctypes.c_int32 * 3)(*[int(d) for d in dims])
+
+
+def make_ordering(kind: int, block=(1, 1, 1), periodic: int = 0) -> lbm_ordering:
+    return lbm_ordering(int(kind), (ctypes.c_int32 * 3)(*[int(b) for b in block]),
+                        int(periodic))
+
+
+def lbm_ordering_keys(dims, ordering: lbm_ordering, keys_dev: int, stream: int) -> None:
+    _check(load().lbm_ordering_keys(_dims(dims), ordering, keys_dev, stream))
+
+
+def lbm_build_sparse(flags_dev: int, dims, ordering: lbm_ordering, stream: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load().lbm_build_sparse(flags_dev, _dims(dims), ordering, stream, ctypes.byref(out)))
+    return out.value
+
+
+def lbm_sparse_info(sparse: int):
+    """(n_fluid, cells_dev, adj_dev, inv_dev) as Python ints."""
+    n = ctypes.c_int64()
+    cells, adj, inv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load().lbm_sparse_info(sparse, ctypes.byref(n), ctypes.byref(cells),
+                                  ctypes.byref(adj), ctypes.byref(inv)))
+    return n.value, cells.value or 0, adj.value or 0, inv.value or 0
+
+
+def lbm_state_create(sparse: int, precision: int, scale_exp: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _check(load().lbm_state_create(sparse, int(precision), int(scale_exp), ctypes.byref(out)))
+    return out.value
+
+
+def lbm_state_set_pdfs(state: int, f_dev: int) -> None:
+    _check(load().lbm_state_set_pdfs(state, f_dev))
+
+
+def lbm_state_get_pdfs(state: int, f_dev: int) -> None:
+    _check(load().lbm_state_get_pdfs(state, f_dev))
+
+
+def lbm_set_damping(state: int, alpha_dev) -> None:
+    _check(load().lbm_set_damping(state, alpha_dev))
+
+
+def lbm_step(state: int, n_steps: int, omega_plus: float, omega_minus: float, force) -> None:
+    f = (ctypes.c_double * 3)(*[float(v) for v in force])
+    _check(load().lbm_step(state, int(n_steps), float(omega_plus), float(omega_minus), f))
+
+
+def lbm_reduce_flux(state: int, axis: int):
+    """(mass, flux) of the most recent step."""
+    m, q = ctypes.c_double(), ctypes.c_double()
+    _check(load().lbm_reduce_flux(state, int(axis), ctypes.byref(m), ctypes.byref(q)))
+    return m.value, q.value
+
+
+def lbm_moments(state: int, rho_dev: int, u_dev: int) -> None:
+    _check(load().lbm_moments(state, rho_dev, u_dev))
+
+
+def lbm_state_steps(state: int) -> int:
+    s = ctypes.c_int64()
+    _check(load().lbm_state_steps(state, ctypes.byref(s)))
+    return s.value
+
+
+def lbm_synchronize(state: int, timeout_s: float = 0.0) -> None:
+    _check(load().lbm_synchronize(state, float(timeout_s)))
+
+
+def lbm_set_timeout(timeout_s: float) -> None:
+    load().lbm_set_timeout(float(timeout_s))
+
+
+def lbm_free(handle) -> None:
+    if handle:
+        load().lbm_free(handle)
+
+
+def lbm_last_error() -> str:
+    return load().lbm_last_error().decode(errors="replace")
+
+
+def lbm_abi_version() -> int:
+    return int(load().lbm_abi_version())

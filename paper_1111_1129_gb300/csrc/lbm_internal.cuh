@@ -1,0 +1,180 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "lbm.h"
+
+namespace lbm {
+
+constexpr uint32_t kMagicSparse = 0x4C53504Bu;
+constexpr uint32_t kMagicState = 0x4C535354u;
+constexpr int kSweepThreads = 256;
+
+// Records a message for lbm_last_error() and returns `status`.
+int fail(int status, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+#define LBM_CUDA_TRY(expr)                                         \
+  do {                                                             \
+    cudaError_t lbm_err_ = (expr);                                 \
+    if (lbm_err_ != cudaSuccess) return ::lbm::cuda_fail(lbm_err_, #expr); \
+  } while (0)
+
+// D3Q19 velocity set: 0 rest; 1..6 axis; 7..18 face diagonals; the odd
+// member of each (odd, odd+1) pair is +c, the even one -c.
+__host__ __device__ __forceinline__ int cx(int q) {
+  switch (q) {
+    case 1: case 7: case 9: case 11: case 13: return 1;
+    case 2: case 8: case 10: case 12: case 14: return -1;
+    default: return 0;
+  }
+}
+__host__ __device__ __forceinline__ int cy(int q) {
+  switch (q) {
+    case 3: case 7: case 10: case 15: case 17: return 1;
+    case 4: case 8: case 9: case 16: case 18: return -1;
+    default: return 0;
+  }
+}
+__host__ __device__ __forceinline__ int cz(int q) {
+  switch (q) {
+    case 5: case 11: case 14: case 15: case 18: return 1;
+    case 6: case 12: case 13: case 16: case 17: return -1;
+    default: return 0;
+  }
+}
+__host__ __device__ __forceinline__ int opp(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+__host__ __device__ __forceinline__ double weight(int q) {
+  return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Numbering-scheme key of box cell (x, y, z) (Sec. 3 "Numbering scheme").
+struct KeySpace {
+  int32_t kind;
+  int64_t nx, ny, nz;
+  int64_t bx, by, bz, nbx, nby, nbz;
+  uint64_t size;  // every key is < size
+};
+
+__host__ __device__ inline uint64_t key_of(const KeySpace& ks, int64_t x, int64_t y, int64_t z) {
+  switch (ks.kind) {
+    case LBM_ORDER_LEX:
+      return (uint64_t)(x + ks.nx * (y + ks.ny * z));
+    case LBM_ORDER_BLOCKED: {
+      const int64_t blk = x / ks.bx + ks.nbx * (y / ks.by + ks.nby * (z / ks.bz));
+      const int64_t loc = x % ks.bx + ks.bx * (y % ks.by + ks.by * (z % ks.bz));
+      return (uint64_t)(blk * (ks.bx * ks.by * ks.bz) + loc);
+    }
+    case LBM_ORDER_MORTON1: {
+      uint64_t k = 0;
+      for (int b = 0; b < 21; ++b) {
+        k |= (((uint64_t)x >> b) & 1u) << (3 * b);
+        k |= (((uint64_t)y >> b) & 1u) << (3 * b + 1);
+        k |= (((uint64_t)z >> b) & 1u) << (3 * b + 2);
+      }
+      return k;
+    }
+    default: {  // LBM_ORDER_MORTON2
+      uint64_t k = 0;
+      for (int g = 0; g < 10; ++g) {
+        k |= (((uint64_t)x >> (2 * g)) & 3u) << (6 * g);
+        k |= (((uint64_t)y >> (2 * g)) & 3u) << (6 * g + 2);
+        k |= (((uint64_t)z >> (2 * g)) & 3u) << (6 * g + 4);
+      }
+      return k;
+    }
+  }
+}
+
+// Inverse of key_of: the box cell of key k, or false if k names no cell of
+// the box (the key space of blocked and Morton orders has gaps).
+__host__ __device__ inline bool cell_of(const KeySpace& ks, uint64_t k, int64_t& x, int64_t& y,
+                                        int64_t& z) {
+  switch (ks.kind) {
+    case LBM_ORDER_LEX: {
+      x = (int64_t)(k % (uint64_t)ks.nx);
+      const uint64_t t = k / (uint64_t)ks.nx;
+      y = (int64_t)(t % (uint64_t)ks.ny);
+      z = (int64_t)(t / (uint64_t)ks.ny);
+      break;
+    }
+    case LBM_ORDER_BLOCKED: {
+      const uint64_t bsz = (uint64_t)(ks.bx * ks.by * ks.bz);
+      const uint64_t blk = k / bsz, loc = k % bsz;
+      const int64_t lx = (int64_t)(loc % (uint64_t)ks.bx);
+      const int64_t ly = (int64_t)((loc / (uint64_t)ks.bx) % (uint64_t)ks.by);
+      const int64_t lz = (int64_t)(loc / (uint64_t)(ks.bx * ks.by));
+      const int64_t ix = (int64_t)(blk % (uint64_t)ks.nbx);
+      const int64_t iy = (int64_t)((blk / (uint64_t)ks.nbx) % (uint64_t)ks.nby);
+      const int64_t iz = (int64_t)(blk / (uint64_t)(ks.nbx * ks.nby));
+      x = ix * ks.bx + lx;
+      y = iy * ks.by + ly;
+      z = iz * ks.bz + lz;
+      break;
+    }
+    case LBM_ORDER_MORTON1: {
+      x = y = z = 0;
+      for (int b = 0; b < 21; ++b) {
+        x |= (int64_t)((k >> (3 * b)) & 1u) << b;
+        y |= (int64_t)((k >> (3 * b + 1)) & 1u) << b;
+        z |= (int64_t)((k >> (3 * b + 2)) & 1u) << b;
+      }
+      break;
+    }
+    default: {
+      x = y = z = 0;
+      for (int g = 0; g < 10; ++g) {
+        x |= (int64_t)((k >> (6 * g)) & 3u) << (2 * g);
+        y |= (int64_t)((k >> (6 * g + 2)) & 3u) << (2 * g);
+        z |= (int64_t)((k >> (6 * g + 4)) & 3u) << (2 * g);
+      }
+      break;
+    }
+  }
+  return k < ks.size && x < ks.nx && y < ks.ny && z < ks.nz;
+}
+
+// Validates dims/ordering and fills the key space; returns LBM_OK or an error.
+// clamp_blocks shrinks blocking factors larger than the box (same order,
+// smaller key space) for the assembly walk.
+int make_key_space(const int32_t dims[3], const lbm_ordering& ord, bool clamp_blocks,
+                   KeySpace* ks);
+
+}  // namespace lbm
+
+struct lbm_sparse {
+  uint32_t magic;
+  int32_t dims[3];
+  lbm_ordering ord;
+  int64_t n;
+  int32_t* cells;  // [n]
+  int32_t* inv;    // [box]
+  int32_t* adj;    // [18 * n]
+  cudaStream_t stream;
+};
+
+struct lbm_state {
+  uint32_t magic;
+  const lbm_sparse* sp;
+  int32_t precision;
+  int32_t scale_exp;
+  void* buf[2];        // PDF grids, [19 * n] elements of the storage type
+  int cur;             // index of the grid holding the current PDFs
+  void* alpha;         // [n] damping in the arithmetic precision, or nullptr
+  double* partials;    // [nblocks * 4] FP64 block sums of the last step
+  int64_t nblocks;
+  double* red_dev;     // [4] final sums
+  double* red_host;    // [4] pinned
+  int64_t steps;
+  double last_force[3];
+  double last_wp, last_wm;
+  cudaEvent_t done;    // recorded to wait for the stream with a time limit
+};
+
+namespace lbm {
+void free_state(lbm_state* st);
+void free_sparse(lbm_sparse* sp);
+}  // namespace lbm

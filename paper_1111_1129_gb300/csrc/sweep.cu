@@ -1,0 +1,633 @@
+// The D3Q19 TRT stream-collide sweep over the sparse representation
+// (Sec. 1: TRT on D3Q19; Sec. 2: sparse representation with implicit bounce
+// back; Sec. 7: pull scheme, structure of arrays, nontemporal stores).
+//
+// One thread updates one fluid cell per step:
+//   gather   g_0 = f[n], g_i = f[adj[i-1][n]]     (pull through the list)
+//   collide  TRT with body force and Brinkman damping, written on the nine
+//            (c, -c) pairs: with s = g_a + g_b, d = g_a - g_b,
+//              f*_a = P + Q,  f*_b = P - Q,
+//              P = (1 - w+)/2 s + w+ e+,   Q = (1 - w-)/2 d + c.V,
+//              w+ e+ = w+ w (rho - 1.5 u.u) + 4.5 w+ w (c.u)^2,
+//              V = 3 w (w- u + (1 - w-/2) F_n),
+//            which is the same update as f* = g - w+(g+ - e+) - w-(g- - e-)
+//            + (1 - w-/2) 3 w c.F_n, with fewer operations;
+//   store    f'[q][n] with streaming (evict-first) stores, the GPU analogue
+//            of the paper's nontemporal stores.
+// The last step of a call also reduces rho and u to FP64 block partials.
+//
+// Storage forms: FP64 / FP32 PDFs, or the deviation d_q = f_q - w_q from
+// the rest state in FP32, FP16 or BF16 (16-bit forms scaled by 2^k).  The
+// collision on deviations is the same formula with rho replaced by
+// rho - 1, because w_q is the equilibrium of rho = 1, u = 0.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <chrono>
+#include <cmath>
+#include <thread>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+namespace {
+
+template <int PREC>
+struct Form;
+template <>
+struct Form<LBM_F64> {
+  using S = double;
+  using C = double;
+  static constexpr bool kShifted = false;
+};
+template <>
+struct Form<LBM_F32> {
+  using S = float;
+  using C = float;
+  static constexpr bool kShifted = false;
+};
+template <>
+struct Form<LBM_F32S> {
+  using S = float;
+  using C = float;
+  static constexpr bool kShifted = true;
+};
+template <>
+struct Form<LBM_F16S> {
+  using S = __half;
+  using C = float;
+  static constexpr bool kShifted = true;
+};
+template <>
+struct Form<LBM_BF16S> {
+  using S = __nv_bfloat16;
+  using C = float;
+  static constexpr bool kShifted = true;
+};
+
+// Per-launch coefficients in the arithmetic precision C.
+template <class C>
+struct Coef {
+  C hp, hm;        // (1 - w+)/2, (1 - w-)/2
+  C one_m_wp;      // 1 - w+
+  C w0p, w1p;      // w+ / 3, w+ / 18
+  C k1, k2;        // 4.5 w+ / 18, 4.5 w+ / 36
+  C a1, b1;        // 3 w- / 18, 3 (1 - w-/2) / 18
+  C F[3], hF[3];   // F, F / 2
+  C bF1[3];        // b1 F (used without damping)
+  C scale, inv_scale;
+};
+
+template <class C>
+Coef<C> make_coef(double wp, double wm, const double F[3], int scale_exp) {
+  Coef<C> k;
+  k.hp = (C)(0.5 * (1.0 - wp));
+  k.hm = (C)(0.5 * (1.0 - wm));
+  k.one_m_wp = (C)(1.0 - wp);
+  k.w0p = (C)(wp / 3.0);
+  k.w1p = (C)(wp / 18.0);
+  k.k1 = (C)(4.5 * wp / 18.0);
+  k.k2 = (C)(4.5 * wp / 36.0);
+  k.a1 = (C)(3.0 * wm / 18.0);
+  const double b1 = 3.0 * (1.0 - 0.5 * wm) / 18.0;
+  k.b1 = (C)b1;
+  for (int d = 0; d < 3; ++d) {
+    k.F[d] = (C)F[d];
+    k.hF[d] = (C)(0.5 * F[d]);
+    k.bF1[d] = (C)(b1 * F[d]);
+  }
+  k.scale = (C)std::ldexp(1.0, scale_exp);
+  k.inv_scale = (C)std::ldexp(1.0, -scale_exp);
+  return k;
+}
+
+// ---- storage conversion -------------------------------------------------
+template <int PREC>
+__device__ __forceinline__ typename Form<PREC>::C decode(typename Form<PREC>::S v,
+                                                         typename Form<PREC>::C inv_scale) {
+  if constexpr (PREC == LBM_F16S) return __half2float(v) * inv_scale;
+  else if constexpr (PREC == LBM_BF16S) return __bfloat162float(v) * inv_scale;
+  else return v;
+}
+
+template <int PREC>
+__device__ __forceinline__ typename Form<PREC>::S encode(typename Form<PREC>::C v,
+                                                         typename Form<PREC>::C scale) {
+  if constexpr (PREC == LBM_F16S) return __float2half_rn(v * scale);
+  else if constexpr (PREC == LBM_BF16S) return __float2bfloat16_rn(v * scale);
+  else return v;
+}
+
+template <int PREC>
+__device__ __forceinline__ typename Form<PREC>::S load_ro(const typename Form<PREC>::S* p) {
+  if constexpr (PREC == LBM_F16S) {
+    return __ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p)));
+  } else if constexpr (PREC == LBM_BF16S) {
+    return __ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p)));
+  } else {
+    return __ldg(p);
+  }
+}
+
+template <int PREC>
+__device__ __forceinline__ void store_stream(typename Form<PREC>::S* p, typename Form<PREC>::S v) {
+  if constexpr (PREC == LBM_F16S) {
+    __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(v));
+  } else if constexpr (PREC == LBM_BF16S) {
+    __stcs(reinterpret_cast<unsigned short*>(p), __bfloat16_as_ushort(v));
+  } else {
+    __stcs(p, v);
+  }
+}
+
+// ---- the collision ----------------------------------------------------------
+// g[19] in: pulled PDFs (or deviations); out: post-collision values.
+template <class C, bool DAMPED>
+__device__ __forceinline__ void collide(C g[19], const Coef<C>& k, C alpha, C& rho_out,
+                                        C u_out[3]) {
+  C s[9], d[9];
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    s[p] = g[2 * p + 1] + g[2 * p + 2];
+    d[p] = g[2 * p + 1] - g[2 * p + 2];
+  }
+  // pairs: 0:(1,2)=+x 1:(3,4)=+y 2:(5,6)=+z 3:(7,8)=(1,1,0) 4:(9,10)=(1,-1,0)
+  // 5:(11,12)=(1,0,1) 6:(13,14)=(1,0,-1) 7:(15,16)=(0,1,1) 8:(17,18)=(0,1,-1)
+  const C rho = g[0] + (((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])) + s[8]);
+  const C jx = ((d[0] + d[3]) + (d[4] + d[5])) + d[6];
+  const C jy = ((d[1] + d[3]) - (d[4] - d[7])) + d[8];
+  const C jz = ((d[2] + d[5]) - (d[6] - d[7])) - d[8];
+  C ux, uy, uz, Vx, Vy, Vz;
+  if constexpr (DAMPED) {
+    const C ia = C(1) / (C(1) + C(0.5) * alpha);
+    ux = (jx + k.hF[0]) * ia;
+    uy = (jy + k.hF[1]) * ia;
+    uz = (jz + k.hF[2]) * ia;
+    Vx = k.a1 * ux + k.b1 * (k.F[0] - alpha * ux);
+    Vy = k.a1 * uy + k.b1 * (k.F[1] - alpha * uy);
+    Vz = k.a1 * uz + k.b1 * (k.F[2] - alpha * uz);
+  } else {
+    ux = jx + k.hF[0];
+    uy = jy + k.hF[1];
+    uz = jz + k.hF[2];
+    Vx = k.a1 * ux + k.bF1[0];
+    Vy = k.a1 * uy + k.bF1[1];
+    Vz = k.a1 * uz + k.bF1[2];
+  }
+  const C usq = ux * ux + uy * uy + uz * uz;
+  const C rp = rho - C(1.5) * usq;
+  const C R1 = k.w1p * rp, R2 = C(0.5) * R1;
+  g[0] = k.one_m_wp * g[0] + k.w0p * rp;
+#define LBM_PAIR(P, CU, CV, R, K, HALF)                    \
+  {                                                        \
+    const C cu_ = (CU);                                    \
+    const C cv_ = HALF ? C(0.5) * (CV) : (CV);             \
+    const C P_ = k.hp * s[P] + (K * (cu_ * cu_) + R);      \
+    const C Q_ = k.hm * d[P] + cv_;                        \
+    g[2 * P + 1] = P_ + Q_;                                \
+    g[2 * P + 2] = P_ - Q_;                                \
+  }
+  LBM_PAIR(0, ux, Vx, R1, k.k1, false)
+  LBM_PAIR(1, uy, Vy, R1, k.k1, false)
+  LBM_PAIR(2, uz, Vz, R1, k.k1, false)
+  LBM_PAIR(3, ux + uy, Vx + Vy, R2, k.k2, true)
+  LBM_PAIR(4, ux - uy, Vx - Vy, R2, k.k2, true)
+  LBM_PAIR(5, ux + uz, Vx + Vz, R2, k.k2, true)
+  LBM_PAIR(6, ux - uz, Vx - Vz, R2, k.k2, true)
+  LBM_PAIR(7, uy + uz, Vy + Vz, R2, k.k2, true)
+  LBM_PAIR(8, uy - uz, Vy - Vz, R2, k.k2, true)
+#undef LBM_PAIR
+  rho_out = rho;
+  u_out[0] = ux;
+  u_out[1] = uy;
+  u_out[2] = uz;
+}
+
+// Fixed-order block reduction of 4 doubles; thread 0 writes out[0..3].
+__device__ __forceinline__ void block_sum4(double v[4], double* out) {
+  __shared__ double sm[kSweepThreads / 32][4];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sm[warp][j] = v[j];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double acc = 0.0;
+#pragma unroll
+    for (int w = 0; w < kSweepThreads / 32; ++w) acc += sm[w][threadIdx.x];
+    out[threadIdx.x] = acc;
+  }
+}
+
+// Gathers the 19 pulled values of cell i.
+template <int PREC>
+__device__ __forceinline__ void gather(const typename Form<PREC>::S* __restrict__ src,
+                                       const int32_t* __restrict__ adj, int32_t n, int32_t i,
+                                       typename Form<PREC>::C inv_scale,
+                                       typename Form<PREC>::C g[19]) {
+  int32_t idx[18];
+#pragma unroll
+  for (int q = 0; q < 18; ++q) idx[q] = __ldcs(adj + q * n + i);
+  g[0] = decode<PREC>(load_ro<PREC>(src + i), inv_scale);
+#pragma unroll
+  for (int q = 1; q < 19; ++q) g[q] = decode<PREC>(load_ro<PREC>(src + idx[q - 1]), inv_scale);
+}
+
+template <int PREC, bool DAMPED, bool REDUCE>
+__global__ void __launch_bounds__(kSweepThreads)
+    sweep_kernel(const typename Form<PREC>::S* __restrict__ src,
+                 typename Form<PREC>::S* __restrict__ dst, const int32_t* __restrict__ adj,
+                 int32_t n, Coef<typename Form<PREC>::C> k,
+                 const typename Form<PREC>::C* __restrict__ alpha, double* __restrict__ partials) {
+  using C = typename Form<PREC>::C;
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < n) {
+    C g[19];
+    gather<PREC>(src, adj, n, i, k.inv_scale, g);
+    C rho, u[3];
+    collide<C, DAMPED>(g, k, DAMPED ? alpha[i] : C(0), rho, u);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) store_stream<PREC>(dst + q * n + i, encode<PREC>(g[q], k.scale));
+    if (REDUCE) {
+      red[0] = (double)rho;
+      red[1] = (double)u[0];
+      red[2] = (double)u[1];
+      red[3] = (double)u[2];
+    }
+  }
+  if (REDUCE) block_sum4(red, partials + 4 * (int64_t)blockIdx.x);
+}
+
+// Per-cell moments of the collision that a step from `src` performs.
+template <int PREC, bool DAMPED>
+__global__ void __launch_bounds__(kSweepThreads)
+    moments_kernel(const typename Form<PREC>::S* __restrict__ src, const int32_t* __restrict__ adj,
+                   int32_t n, Coef<typename Form<PREC>::C> k,
+                   const typename Form<PREC>::C* __restrict__ alpha, double* __restrict__ rho_out,
+                   double* __restrict__ u_out) {
+  using C = typename Form<PREC>::C;
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  if (i >= n) return;
+  C g[19];
+  gather<PREC>(src, adj, n, i, k.inv_scale, g);
+  C rho, u[3];
+  collide<C, DAMPED>(g, k, DAMPED ? alpha[i] : C(0), rho, u);
+  rho_out[i] = Form<PREC>::kShifted ? 1.0 + (double)rho : (double)rho;
+  u_out[i] = (double)u[0];
+  u_out[n + i] = (double)u[1];
+  u_out[2 * (int64_t)n + i] = (double)u[2];
+}
+
+// Final fixed-order sum of the block partials: out[j] = sum_b part[4 b + j].
+__global__ void __launch_bounds__(1024)
+    final_sum_kernel(const double* __restrict__ part, int64_t nblocks, double* out) {
+  __shared__ double sm[1024][4];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t b = threadIdx.x; b < nblocks; b += 1024)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] += part[4 * b + j];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sm[threadIdx.x][j] = acc[j];
+  __syncthreads();
+  for (int s = 512; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sm[threadIdx.x][j] += sm[threadIdx.x + s][j];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) out[threadIdx.x] = sm[0][threadIdx.x];
+}
+
+template <int PREC>
+__global__ void set_pdfs_kernel(typename Form<PREC>::S* __restrict__ dst,
+                                const double* __restrict__ f, int32_t n, double scale,
+                                int from_rest) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 19 * (int64_t)n) return;
+  const int q = (int)(t / n);
+  const double w = weight(q);
+  const double v = from_rest ? w : f[t];
+  using C = typename Form<PREC>::C;
+  C c;
+  if constexpr (Form<PREC>::kShifted) c = (C)(v - w);
+  else c = (C)v;
+  dst[t] = encode<PREC>(c, (C)scale);
+}
+
+template <int PREC>
+__global__ void get_pdfs_kernel(const typename Form<PREC>::S* __restrict__ src, double* f,
+                                int32_t n, double inv_scale) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 19 * (int64_t)n) return;
+  const int q = (int)(t / n);
+  using C = typename Form<PREC>::C;
+  const double v = (double)decode<PREC>(src[t], (C)inv_scale);
+  f[t] = Form<PREC>::kShifted ? weight(q) + v : v;
+}
+
+template <class C>
+__global__ void set_alpha_kernel(C* dst, const double* a, int32_t n) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (C)a[i];
+}
+
+size_t storage_bytes(int prec) {
+  switch (prec) {
+    case LBM_F64: return 8;
+    case LBM_F32: case LBM_F32S: return 4;
+    default: return 2;
+  }
+}
+size_t compute_bytes(int prec) { return prec == LBM_F64 ? 8 : 4; }
+
+double g_timeout_s = 600.0;
+
+int wait_event(cudaEvent_t ev, cudaStream_t stream, double timeout_s) {
+  LBM_CUDA_TRY(cudaEventRecord(ev, stream));
+  const double limit = timeout_s > 0 ? timeout_s : g_timeout_s;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return LBM_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "cudaEventQuery");
+    const double el =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > limit)
+      return fail(LBM_ETIMEOUT, "queued work still running after %.1f s", limit);
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+bool valid_state(const lbm_state* st) { return st && st->magic == kMagicState; }
+
+template <int PREC>
+int launch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3]) {
+  using S = typename Form<PREC>::S;
+  using C = typename Form<PREC>::C;
+  const int32_t n = (int32_t)st->sp->n;
+  const cudaStream_t stream = st->sp->stream;
+  const Coef<C> k = make_coef<C>(wp, wm, F, st->scale_exp);
+  const unsigned grid = (unsigned)st->nblocks;
+  const C* alpha = (const C*)st->alpha;
+  for (int32_t t = 0; t < n_steps; ++t) {
+    const S* src = (const S*)st->buf[st->cur];
+    S* dst = (S*)st->buf[st->cur ^ 1];
+    const bool last = t == n_steps - 1;
+    if (n > 0) {
+      if (alpha) {
+        if (last) sweep_kernel<PREC, true, true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, st->partials);
+        else sweep_kernel<PREC, true, false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, st->partials);
+      } else {
+        if (last) sweep_kernel<PREC, false, true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, st->partials);
+        else sweep_kernel<PREC, false, false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, st->partials);
+      }
+    }
+    st->cur ^= 1;
+  }
+  LBM_CUDA_TRY(cudaGetLastError());
+  return LBM_OK;
+}
+
+template <int PREC>
+int launch_moments(const lbm_state* st, double* rho, double* u) {
+  using S = typename Form<PREC>::S;
+  using C = typename Form<PREC>::C;
+  const int32_t n = (int32_t)st->sp->n;
+  if (n == 0) return LBM_OK;
+  const Coef<C> k = make_coef<C>(st->last_wp, st->last_wm, st->last_force, st->scale_exp);
+  const S* prev = (const S*)st->buf[st->cur ^ 1];
+  const C* alpha = (const C*)st->alpha;
+  if (alpha)
+    moments_kernel<PREC, true><<<(unsigned)st->nblocks, kSweepThreads, 0, st->sp->stream>>>(prev, st->sp->adj, n, k, alpha, rho, u);
+  else
+    moments_kernel<PREC, false><<<(unsigned)st->nblocks, kSweepThreads, 0, st->sp->stream>>>(prev, st->sp->adj, n, k, alpha, rho, u);
+  LBM_CUDA_TRY(cudaGetLastError());
+  return LBM_OK;
+}
+
+template <int PREC>
+int launch_set(lbm_state* st, const double* f, int from_rest) {
+  const int64_t total = 19 * st->sp->n;
+  if (total == 0) return LBM_OK;
+  set_pdfs_kernel<PREC><<<(unsigned)((total + 255) / 256), 256, 0, st->sp->stream>>>(
+      (typename Form<PREC>::S*)st->buf[st->cur], f, (int32_t)st->sp->n,
+      std::ldexp(1.0, st->scale_exp), from_rest);
+  LBM_CUDA_TRY(cudaGetLastError());
+  return LBM_OK;
+}
+
+template <int PREC>
+int launch_get(const lbm_state* st, double* f) {
+  const int64_t total = 19 * st->sp->n;
+  if (total == 0) return LBM_OK;
+  get_pdfs_kernel<PREC><<<(unsigned)((total + 255) / 256), 256, 0, st->sp->stream>>>(
+      (const typename Form<PREC>::S*)st->buf[st->cur], f, (int32_t)st->sp->n,
+      std::ldexp(1.0, -st->scale_exp));
+  LBM_CUDA_TRY(cudaGetLastError());
+  return LBM_OK;
+}
+
+#define LBM_DISPATCH(prec, fn, ...)                          \
+  switch (prec) {                                            \
+    case LBM_F64: return fn<LBM_F64>(__VA_ARGS__);           \
+    case LBM_F32: return fn<LBM_F32>(__VA_ARGS__);           \
+    case LBM_F32S: return fn<LBM_F32S>(__VA_ARGS__);         \
+    case LBM_F16S: return fn<LBM_F16S>(__VA_ARGS__);         \
+    default: return fn<LBM_BF16S>(__VA_ARGS__);              \
+  }
+
+int dispatch_set(lbm_state* st, const double* f, int from_rest) {
+  LBM_DISPATCH(st->precision, launch_set, st, f, from_rest)
+}
+int dispatch_get(const lbm_state* st, double* f) { LBM_DISPATCH(st->precision, launch_get, st, f) }
+int dispatch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3]) {
+  LBM_DISPATCH(st->precision, launch_steps, st, n_steps, wp, wm, F)
+}
+int dispatch_moments(const lbm_state* st, double* rho, double* u) {
+  LBM_DISPATCH(st->precision, launch_moments, st, rho, u)
+}
+
+}  // namespace
+
+void free_state(lbm_state* st) {
+  if (!st) return;
+  const cudaStream_t s = st->sp ? st->sp->stream : nullptr;
+  cudaStreamSynchronize(s);
+  for (void* p : {st->buf[0], st->buf[1], st->alpha, (void*)st->partials, (void*)st->red_dev})
+    if (p) cudaFree(p);
+  if (st->red_host) cudaFreeHost(st->red_host);
+  if (st->done) cudaEventDestroy(st->done);
+  st->magic = 0;
+  delete st;
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+extern "C" int lbm_state_create(const lbm_sparse* sp, int32_t precision, int32_t scale_exp,
+                                lbm_state** out) {
+  clear_error();
+  if (!out) return fail(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!sp || sp->magic != kMagicSparse) return fail(LBM_EINVAL, "not a sparse handle");
+  if (precision < LBM_F64 || precision > LBM_BF16S)
+    return fail(LBM_EINVAL, "unknown precision %d", precision);
+  if ((precision == LBM_F16S || precision == LBM_BF16S) && (scale_exp < 0 || scale_exp > 40))
+    return fail(LBM_EINVAL, "scale_exp %d outside [0, 40]", scale_exp);
+  lbm_state* st = new lbm_state{};
+  st->magic = kMagicState;
+  st->sp = sp;
+  st->precision = precision;
+  st->scale_exp = (precision == LBM_F16S || precision == LBM_BF16S) ? scale_exp : 0;
+  const int64_t n = sp->n;
+  st->nblocks = (n + kSweepThreads - 1) / kSweepThreads;
+  if (st->nblocks < 1) st->nblocks = 1;
+  const size_t bytes = storage_bytes(precision) * 19 * (size_t)(n > 0 ? n : 1);
+  bool ok = cudaMalloc(&st->buf[0], bytes) == cudaSuccess &&
+            cudaMalloc(&st->buf[1], bytes) == cudaSuccess &&
+            cudaMalloc(&st->partials, sizeof(double) * 4 * st->nblocks) == cudaSuccess &&
+            cudaMalloc(&st->red_dev, sizeof(double) * 4) == cudaSuccess &&
+            cudaMallocHost(&st->red_host, sizeof(double) * 4) == cudaSuccess &&
+            cudaEventCreateWithFlags(&st->done, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_state(st);
+    return fail(LBM_ENOMEM, "state allocation of 2 x %zu bytes failed", bytes);
+  }
+  int rc = dispatch_set(st, nullptr, 1);
+  if (rc == LBM_OK) {
+    const cudaError_t e = cudaMemsetAsync(st->buf[1], 0, bytes, sp->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync");
+  }
+  if (rc != LBM_OK) {
+    free_state(st);
+    return rc;
+  }
+  *out = st;
+  return LBM_OK;
+}
+
+extern "C" int lbm_state_set_pdfs(lbm_state* st, const double* f_dev) {
+  clear_error();
+  if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  if (!f_dev) return fail(LBM_EINVAL, "f_dev is NULL");
+  st->steps = 0;
+  return dispatch_set(st, f_dev, 0);
+}
+
+extern "C" int lbm_state_get_pdfs(const lbm_state* st, double* f_dev) {
+  clear_error();
+  if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  if (!f_dev) return fail(LBM_EINVAL, "f_dev is NULL");
+  return dispatch_get(st, f_dev);
+}
+
+extern "C" int lbm_set_damping(lbm_state* st, const double* alpha_dev) {
+  clear_error();
+  if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  if (!alpha_dev) {
+    if (st->alpha) {
+      cudaStreamSynchronize(st->sp->stream);
+      cudaFree(st->alpha);
+    }
+    st->alpha = nullptr;
+    return LBM_OK;
+  }
+  const int64_t n = st->sp->n;
+  if (!st->alpha) {
+    if (cudaMalloc(&st->alpha, compute_bytes(st->precision) * (size_t)(n > 0 ? n : 1)) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      st->alpha = nullptr;
+      return fail(LBM_ENOMEM, "damping field allocation failed");
+    }
+  }
+  if (n > 0) {
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (st->precision == LBM_F64)
+      set_alpha_kernel<double><<<grid, 256, 0, st->sp->stream>>>((double*)st->alpha, alpha_dev, (int32_t)n);
+    else
+      set_alpha_kernel<float><<<grid, 256, 0, st->sp->stream>>>((float*)st->alpha, alpha_dev, (int32_t)n);
+    LBM_CUDA_TRY(cudaGetLastError());
+  }
+  return LBM_OK;
+}
+
+extern "C" int lbm_step(lbm_state* st, int32_t n_steps, double omega_plus, double omega_minus,
+                        const double force[3]) {
+  clear_error();
+  if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  if (n_steps < 0) return fail(LBM_EINVAL, "n_steps = %d < 0", n_steps);
+  if (!(omega_plus > 0.0 && omega_plus < 2.0) || !(omega_minus > 0.0 && omega_minus < 2.0))
+    return fail(LBM_EINVAL, "relaxation rates must lie in (0, 2): %g, %g", omega_plus, omega_minus);
+  if (!force) return fail(LBM_EINVAL, "force is NULL");
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(force[d])) return fail(LBM_EINVAL, "force[%d] is not finite", d);
+  if (n_steps == 0) return LBM_OK;
+  const int rc = dispatch_steps(st, n_steps, omega_plus, omega_minus, force);
+  if (rc != LBM_OK) return rc;
+  st->steps += n_steps;
+  st->last_wp = omega_plus;
+  st->last_wm = omega_minus;
+  for (int d = 0; d < 3; ++d) st->last_force[d] = force[d];
+  return LBM_OK;
+}
+
+extern "C" int lbm_reduce_flux(lbm_state* st, int32_t axis, double* mass_out, double* flux_out) {
+  clear_error();
+  if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  if (axis < 0 || axis > 2) return fail(LBM_EINVAL, "axis %d outside {0,1,2}", axis);
+  if (st->steps < 1) return fail(LBM_EINVAL, "no step taken yet");
+  const cudaStream_t stream = st->sp->stream;
+  const int64_t n = st->sp->n;
+  if (n > 0) {
+    final_sum_kernel<<<1, 1024, 0, stream>>>(st->partials, st->nblocks, st->red_dev);
+    LBM_CUDA_TRY(cudaGetLastError());
+    LBM_CUDA_TRY(cudaMemcpyAsync(st->red_host, st->red_dev, sizeof(double) * 4,
+                                 cudaMemcpyDeviceToHost, stream));
+    const int rc = wait_event(st->done, stream, 0.0);
+    if (rc != LBM_OK) return rc;
+  } else {
+    for (int j = 0; j < 4; ++j) st->red_host[j] = 0.0;
+  }
+  const bool shifted = st->precision != LBM_F64 && st->precision != LBM_F32;
+  const double mass = shifted ? (double)n + st->red_host[0] : st->red_host[0];
+  const double flux = n > 0 ? st->red_host[1 + axis] / (double)n : 0.0;
+  if (!std::isfinite(mass) || !std::isfinite(flux))
+    return fail(LBM_ENONFINITE, "non-finite mass (%g) or flux (%g)", mass, flux);
+  if (mass_out) *mass_out = mass;
+  if (flux_out) *flux_out = flux;
+  return LBM_OK;
+}
+
+extern "C" int lbm_moments(const lbm_state* st, double* rho_dev, double* u_dev) {
+  clear_error();
+  if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  if (!rho_dev || !u_dev) return fail(LBM_EINVAL, "rho_dev / u_dev is NULL");
+  if (st->steps < 1) return fail(LBM_EINVAL, "no step taken yet");
+  return dispatch_moments(st, rho_dev, u_dev);
+}
+
+extern "C" int lbm_state_steps(const lbm_state* st, int64_t* steps) {
+  clear_error();
+  if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  if (steps) *steps = st->steps;
+  return LBM_OK;
+}
+
+extern "C" int lbm_synchronize(const lbm_state* st, double timeout_s) {
+  clear_error();
+  if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  return wait_event(st->done, st->sp->stream, timeout_s);
+}
+
+extern "C" void lbm_set_timeout(double timeout_s) {
+  if (timeout_s > 0) g_timeout_s = timeout_s;
+}

@@ -1,0 +1,189 @@
+"""PyTorch-facing wrapper of the C ABI: sparse lattices and solver states.
+
+PyTorch supplies device memory for inputs and outputs and the CUDA stream;
+every step of the path runs in the library's kernels.  Names follow the C
+functions (``lbm_build_sparse`` -> :class:`SparseLattice`, ``lbm_step`` ->
+:meth:`LBMState.step`, ...).
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import capi
+
+ORDERINGS = {"lex": capi.LBM_ORDER_LEX, "blocked": capi.LBM_ORDER_BLOCKED,
+             "morton1": capi.LBM_ORDER_MORTON1, "morton2": capi.LBM_ORDER_MORTON2}
+PRECISIONS = {"f64": capi.LBM_F64, "f32": capi.LBM_F32, "f32s": capi.LBM_F32S,
+              "f16s": capi.LBM_F16S, "bf16s": capi.LBM_BF16S}
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f32s": 4, "f16s": 2, "bf16s": 2}
+
+
+def omega_minus(omega_plus: float, magic: float = 3.0 / 16.0) -> float:
+    """Odd relaxation rate from the even one and the TRT magic parameter
+    Lambda = (1/w+ - 1/2)(1/w- - 1/2); Lambda = 3/16 puts bounce-back walls
+    exactly half-way between nodes."""
+    return 1.0 / (0.5 + magic / (1.0 / omega_plus - 0.5))
+
+
+class _DeviceView:
+    """Borrowed device buffer exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
+def _borrow(ptr: int, shape, typestr: str, dtype) -> torch.Tensor:
+    if ptr == 0 or math.prod(shape) == 0:
+        return torch.empty(shape, dtype=dtype, device="cuda")
+    return torch.as_tensor(_DeviceView(ptr, shape, typestr), device="cuda")
+
+
+def _stream_handle(stream) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def ordering_keys(dims, ordering: str = "lex", block=(8, 8, 8), stream=None) -> torch.Tensor:
+    """Numbering-scheme key of every box cell, shape [nz, ny, nx], uint64
+    values stored in an int64 tensor."""
+    nx, ny, nz = (int(d) for d in dims)
+    keys = torch.empty((nz, ny, nx), dtype=torch.int64, device="cuda")
+    capi.lbm_ordering_keys((nx, ny, nz), capi.make_ordering(ORDERINGS[ordering], block),
+                           keys.data_ptr(), _stream_handle(stream))
+    return keys
+
+
+class SparseLattice:
+    """Sparse representation of a voxelised domain (``lbm_build_sparse``).
+
+    flags: uint8 tensor [nz, ny, nx] (0 fluid, 1 solid), on the GPU or the
+    host (host flags are copied to the device first)."""
+
+    def __init__(self, flags: torch.Tensor, ordering: str = "lex", block=(8, 8, 8),
+                 periodic: int = 0, stream=None):
+        if flags.dtype != torch.uint8 or flags.dim() != 3:
+            raise ValueError("flags must be a uint8 tensor [nz, ny, nx]")
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        flags = flags.to("cuda", non_blocking=True).contiguous()
+        nz, ny, nx = flags.shape
+        self.dims = (nx, ny, nz)
+        self.ordering = ordering
+        self.block = tuple(block)
+        self.periodic = int(periodic)
+        self._handle = None
+        self._handle = capi.lbm_build_sparse(
+            flags.data_ptr(), self.dims,
+            capi.make_ordering(ORDERINGS[ordering], block, periodic),
+            int(self.stream.cuda_stream))
+        self.n, self._cells, self._adj, self._inv = capi.lbm_sparse_info(self._handle)
+
+    @property
+    def handle(self) -> int:
+        return self._handle
+
+    def cells(self) -> torch.Tensor:
+        """Copy of cells[N] (box index of each fluid cell, in order)."""
+        return _borrow(self._cells, (self.n,), "<i4", torch.int32).clone()
+
+    def adjacency(self) -> torch.Tensor:
+        """Copy of adj[18, N]."""
+        return _borrow(self._adj, (18, self.n), "<i4", torch.int32).clone()
+
+    def inverse(self) -> torch.Tensor:
+        """Copy of inv[nz, ny, nx] (fluid index or -1)."""
+        nx, ny, nz = self.dims
+        return _borrow(self._inv, (nz, ny, nx), "<i4", torch.int32).clone()
+
+    def gather(self, dense: torch.Tensor) -> torch.Tensor:
+        """Box-layout field [..., nz, ny, nx] -> fluid order [..., N]."""
+        idx = self.cells().long()
+        return dense.reshape(dense.shape[:-3] + (-1,))[..., idx]
+
+    def close(self):
+        if self._handle:
+            capi.lbm_free(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LBMState:
+    """Solver state: PDFs in one of the storage forms (``lbm_state_create``)."""
+
+    def __init__(self, lattice: SparseLattice, precision: str = "f64", scale_exp: int = 0):
+        self.lattice = lattice
+        self.precision = precision
+        self.scale_exp = int(scale_exp)
+        self._handle = None
+        self._handle = capi.lbm_state_create(lattice.handle, PRECISIONS[precision],
+                                             self.scale_exp)
+
+    @property
+    def handle(self) -> int:
+        return self._handle
+
+    @property
+    def n(self) -> int:
+        return self.lattice.n
+
+    def step(self, n_steps: int, omega_plus: float, omega_minus: float, force) -> None:
+        capi.lbm_step(self._handle, n_steps, omega_plus, omega_minus, force)
+
+    def reduce_flux(self, axis: int):
+        """(mass, mean axial velocity) of the most recent step, FP64."""
+        return capi.lbm_reduce_flux(self._handle, axis)
+
+    def moments(self):
+        """(rho [N], u [3, N]) of the most recent step's collision, FP64."""
+        rho = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        u = torch.empty((3, self.n), dtype=torch.float64, device="cuda")
+        capi.lbm_moments(self._handle, rho.data_ptr(), u.data_ptr())
+        return rho, u
+
+    def get_pdfs(self) -> torch.Tensor:
+        f = torch.empty((19, self.n), dtype=torch.float64, device="cuda")
+        capi.lbm_state_get_pdfs(self._handle, f.data_ptr())
+        return f
+
+    def set_pdfs(self, f: torch.Tensor) -> None:
+        f = f.to(device="cuda", dtype=torch.float64).contiguous()
+        if f.shape != (19, self.n):
+            raise ValueError(f"expected PDFs of shape (19, {self.n})")
+        capi.lbm_state_set_pdfs(self._handle, f.data_ptr())
+        self._keep = f
+
+    def set_damping(self, alpha) -> None:
+        if alpha is None:
+            capi.lbm_set_damping(self._handle, None)
+            return
+        a = alpha.to(device="cuda", dtype=torch.float64).contiguous()
+        if a.shape != (self.n,):
+            raise ValueError(f"expected damping of shape ({self.n},)")
+        capi.lbm_set_damping(self._handle, a.data_ptr())
+        self._keep_alpha = a
+
+    @property
+    def steps(self) -> int:
+        return capi.lbm_state_steps(self._handle)
+
+    def synchronize(self, timeout_s: float = 0.0) -> None:
+        capi.lbm_synchronize(self._handle, timeout_s)
+
+    def close(self):
+        if self._handle:
+            capi.lbm_free(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

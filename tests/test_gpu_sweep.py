@@ -1,0 +1,213 @@
+"""FP64 stream-collide sweep on the GPU vs the CPU oracle (Sec. 1, 2, 7).
+
+Tolerance: FP64 PDFs agree with the oracle to 1e-12 of max |f| (the two
+sides sum in different orders; round-off is ~1e-16 per step).  Integer
+outputs (step counts) and the FP64 results across orderings are compared
+bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1111_1129_gb300 import LBMState, SparseLattice, build, capi, inputs, omega_minus
+
+pytestmark = pytest.mark.gpu
+
+WP = 1.0 / 0.8
+WM = omega_minus(WP)
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    capi.load()
+
+
+def _gpu_run(flags, periodic, steps, F, ordering="lex", block=(8, 8, 8), precision="f64",
+             alpha_dense=None, f0_dense=None):
+    lat = SparseLattice(torch.from_numpy(flags).cuda(), ordering, block, periodic)
+    st = LBMState(lat, precision)
+    cells = lat.cells().cpu().numpy()
+    if f0_dense is not None:
+        st.set_pdfs(torch.from_numpy(oracle.to_sparse(f0_dense, cells).copy()))
+    if alpha_dense is not None:
+        st.set_damping(torch.from_numpy(alpha_dense.reshape(-1)[cells].copy()))
+    st.step(steps, WP, WM, F)
+    return lat, st, cells
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("shape", [(2, 2, 2), (3, 4, 5), (6, 6, 6), (5, 1, 3)])
+@pytest.mark.parametrize("periodic", range(8))
+def test_tiny_boxes_random_state_parity(shape, periodic):
+    """Brute force on tiny boxes: random flags, random initial PDFs, random
+    damping, 1-10 steps, every periodicity mask."""
+    rng = np.random.default_rng(hash((shape, periodic)) % 2**32)
+    flags = (rng.random(shape) < 0.25).astype(np.uint8)
+    if (flags == 0).sum() == 0:
+        flags[0, 0, 0] = 0
+    f0 = oracle.rest_state(flags) * (1 + 0.05 * rng.standard_normal((19,) + shape))
+    alpha = 0.05 * rng.random(shape)
+    F = 1e-3 * rng.standard_normal(3)
+    for steps in (1, 3, 10):
+        lat, st, cells = _gpu_run(flags, periodic, steps, F, alpha_dense=alpha, f0_dense=f0)
+        f_ref, obs, rho_ref, u_ref = oracle.run(flags, periodic, WP, WM, F, steps, alpha=alpha,
+                                                f=f0)
+        got = st.get_pdfs().cpu().numpy()
+        assert _rel(got, oracle.to_sparse(f_ref, cells)) < TOL
+        rho, u = st.moments()
+        np.testing.assert_allclose(rho.cpu().numpy(), oracle.to_sparse(rho_ref, cells),
+                                   rtol=0, atol=1e-13)
+        np.testing.assert_allclose(u.cpu().numpy(), oracle.to_sparse(u_ref, cells), rtol=0,
+                                   atol=1e-13 * max(np.abs(u_ref).max(), 1e-30))
+        mass, flux = st.reduce_flux(2)
+        assert abs(mass - obs[-1, 0]) < 1e-13 * abs(obs[-1, 0])
+        assert abs(flux - obs[-1, 3] / lat.n) < 1e-13 * max(np.abs(u_ref).max(), 1e-30)
+        st.close()
+        lat.close()
+
+
+def test_small_bed_1000_steps_parity():
+    """The 32x32x64 packed bed, lexicographic order, 1000 FP64 steps from
+    rest with F = 1e-6 along z."""
+    bed = inputs.bed_small(0)
+    F = (0.0, 0.0, 1e-6)
+    steps = 1000
+    lat, st, cells = _gpu_run(bed.flags, bed.periodic, steps, F)
+    f_ref, obs, rho_ref, u_ref = oracle.run(bed.flags, bed.periodic, WP, WM, F, steps)
+    got = st.get_pdfs().cpu().numpy()
+    err = _rel(got, oracle.to_sparse(f_ref, cells))
+    assert err < TOL, err
+    rho, u = st.moments()
+    u = u.cpu().numpy()
+    uref = oracle.to_sparse(u_ref, cells)
+    assert np.max(np.abs(u - uref)) < 1e-9 * np.max(np.abs(uref))
+    mass, flux = st.reduce_flux(2)
+    assert abs(mass - obs[-1, 0]) < 1e-12 * obs[-1, 0]
+    assert abs(flux - obs[-1, 3] / bed.n_fluid) < 1e-9 * abs(flux)
+    assert st.steps == steps
+    st.close()
+    lat.close()
+
+
+def test_orderings_give_bitwise_identical_fields():
+    """The per-cell arithmetic does not depend on the cell order, so every
+    numbering scheme yields the same FP64 field, bit for bit."""
+    bed = inputs.bed_small(2)
+    F = (0.0, 0.0, 1e-5)
+    ref = None
+    for ordering, block in [("lex", (1, 1, 1)), ("blocked", (8, 8, 8)), ("blocked", (4, 2, 16)),
+                            ("morton1", (1, 1, 1)), ("morton2", (1, 1, 1))]:
+        lat, st, cells = _gpu_run(bed.flags, bed.periodic, 100, F, ordering, block)
+        dense = np.zeros((19, bed.flags.size))
+        dense[:, cells] = st.get_pdfs().cpu().numpy()
+        if ref is None:
+            ref = dense
+        else:
+            np.testing.assert_array_equal(dense, ref)
+        st.close()
+        lat.close()
+
+
+def test_damped_bed_parity():
+    bed = inputs.packed_bed((24, 20, 28), 2, 18.0, 3.0, 0.45, 5)
+    alpha = inputs.alpha_field(bed.dims, seed=5)
+    F = (0.0, 0.0, 1e-5)
+    lat, st, cells = _gpu_run(bed.flags, bed.periodic, 200, F, "morton1", alpha_dense=alpha)
+    f_ref, obs, _, _ = oracle.run(bed.flags, bed.periodic, WP, WM, F, 200, alpha=alpha)
+    assert _rel(st.get_pdfs().cpu().numpy(), oracle.to_sparse(f_ref, cells)) < TOL
+    mass, flux = st.reduce_flux(2)
+    assert abs(flux - obs[-1, 3] / bed.n_fluid) < 1e-9 * abs(flux)
+    st.close()
+    lat.close()
+
+
+def test_reductions_are_deterministic_and_need_a_step():
+    bed = inputs.bed_small(0)
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "blocked", (8, 8, 8), bed.periodic)
+    vals = []
+    for _ in range(2):
+        st = LBMState(lat, "f64")
+        with pytest.raises(capi.LbmError):
+            st.reduce_flux(2)
+        st.step(50, WP, WM, (0, 0, 1e-6))
+        vals.append(st.reduce_flux(2))
+        with pytest.raises(capi.LbmError):
+            st.reduce_flux(3)
+        st.close()
+    assert vals[0] == vals[1]
+    lat.close()
+
+
+def test_state_roundtrip_and_rest_init():
+    bed = inputs.bed_small(0)
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "lex", periodic=bed.periodic)
+    st = LBMState(lat, "f64")
+    _, w, _ = oracle.velocity_set()
+    f = st.get_pdfs().cpu().numpy()
+    np.testing.assert_array_equal(f, np.repeat(w[:, None], lat.n, axis=1))
+    rng = np.random.default_rng(0)
+    f1 = rng.random((19, lat.n))
+    st.set_pdfs(torch.from_numpy(f1))
+    np.testing.assert_array_equal(st.get_pdfs().cpu().numpy(), f1)
+    assert st.steps == 0
+    st.close()
+    lat.close()
+
+
+def test_empty_domain_steps():
+    flags = np.ones((3, 4, 5), np.uint8)
+    lat = SparseLattice(torch.from_numpy(flags).cuda(), "lex")
+    st = LBMState(lat, "f64")
+    st.step(3, WP, WM, (0, 0, 1e-6))
+    assert st.reduce_flux(0) == (0.0, 0.0)
+    st.close()
+    lat.close()
+
+
+def test_step_argument_validation():
+    bed = inputs.bed_small(0)
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "lex", periodic=bed.periodic)
+    st = LBMState(lat, "f64")
+    for bad in [dict(n_steps=-1), dict(omega_plus=2.0), dict(omega_minus=0.0),
+                dict(force=(0.0, float("nan"), 0.0))]:
+        args = dict(n_steps=1, omega_plus=WP, omega_minus=WM, force=(0, 0, 1e-6))
+        args.update(bad)
+        with pytest.raises(capi.LbmError) as ei:
+            st.step(**args)
+        assert ei.value.status == capi.LBM_EINVAL
+    st.close()
+    lat.close()
+
+
+def test_large_bed_sampled_parity():
+    """The 1024x256x256 bed at full size, 8^3 blocked order, in the launch
+    configuration the benchmark times: adjacency bit-exact against the
+    oracle, and one step checked cell by cell on a sample with the oracle's
+    collision applied to the oracle's own pull of the GPU's previous state."""
+    bed = inputs.bed_large(0)
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "blocked", (8, 8, 8), bed.periodic)
+    cells, _, adj = oracle.build_sparse(bed.flags, oracle.ORDER_BLOCKED, (8, 8, 8), bed.periodic)
+    np.testing.assert_array_equal(lat.cells().cpu().numpy(), cells)
+    np.testing.assert_array_equal(lat.adjacency().cpu().numpy(), adj)
+    st = LBMState(lat, "f64")
+    F = (1e-6, 0.0, 0.0)
+    st.step(20, WP, WM, F)
+    prev = st.get_pdfs().cpu().numpy().ravel()
+    st.step(1, WP, WM, F)
+    nxt = st.get_pdfs().cpu().numpy()
+    mass, _ = st.reduce_flux(0)
+    assert abs(mass - lat.n) < 1e-10 * lat.n
+    rng = np.random.default_rng(0)
+    sample = rng.choice(lat.n, 2000, replace=False)
+    for n in sample:
+        g = np.concatenate([[prev[n]], prev[adj[:, n]]])
+        fo, _, _ = oracle.collide(g, F, 0.0, WP, WM)
+        np.testing.assert_allclose(nxt[:, n], fo, rtol=0, atol=1e-15)
+    st.close()
+    lat.close()
