@@ -197,6 +197,39 @@ int lbm_state_steps(const lbm_state* st, int64_t* steps);
 int lbm_synchronize(const lbm_state* st, double timeout_s);
 void lbm_set_timeout(double timeout_s);
 
+/*
+ * One FP64 time step that allocates nothing.  The paper has no counterpart;
+ * this entry point exists for callers that cannot allocate device memory --
+ * for example a host application that owns all of the GPU's memory and
+ * hands this library only the arrays it works on, or a time-stepping loop
+ * with a fixed memory budget that cannot take the device-wide
+ * synchronisation and latency of a cudaMalloc.  It performs exactly what one
+ * step of lbm_step does on an LBM_F64 state and what lbm_reduce_flux then
+ * sums, on caller-owned arrays:
+ *   f_src_dev: device FP64[19*N] PDFs before the step (layout above), read.
+ *   f_dst_dev: device FP64[19*N] PDFs after the step, written; must not
+ *              overlap f_src_dev.
+ *   adj_dev:   device int32[18*N] adjacency, e.g. from lbm_sparse_info.
+ *   n_fluid:   N, 0 <= N <= 16,777,216 (LBM_EINVAL beyond).
+ *   alpha_dev: device FP64[N] Brinkman damping, or NULL for none.
+ *   sums_dev:  device FP64[4], written: sum rho, sum u_x, sum u_y, sum u_z
+ *              of this step's collision (flux = sum u_axis / N).
+ *   stream:    cudaStream_t the work is queued on (asynchronous).
+ * Its only scratch, the FP64 block partial sums (at most 65,536 blocks of
+ * 256 cells), lives in a fixed 2 MiB static device array that every GPU
+ * loading this library holds until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.
+ * Every call shares the array and it keeps the last call's contents; each
+ * call overwrites the entries it reads, so nothing needs clearing, but two
+ * calls that overlap on the same GPU (for example on two streams) race on
+ * it.  Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+int lbm_step_f64_noalloc(const double* f_src_dev, double* f_dst_dev, const int32_t* adj_dev,
+                         int64_t n_fluid, double omega_plus, double omega_minus,
+                         const double force[3], const double* alpha_dev, double* sums_dev,
+                         void* stream);
+
 /* Release a handle returned by this library (sparse or state); NULL is a
  * no-op.  Waits for the handle's stream before freeing. */
 void lbm_free(void* handle);

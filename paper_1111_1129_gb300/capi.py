@@ -43,6 +43,7 @@ SIGNATURES = {
     "lbm_state_steps": (ctypes.c_int, [_vp, _vp]),
     "lbm_synchronize": (ctypes.c_int, [_vp, _d]),
     "lbm_set_timeout": (None, [_d]),
+    "lbm_step_f64_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i64, _d, _d, _vp, _vp, _vp, _vp]),
     "lbm_free": (None, [_vp]),
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_abi_version": (ctypes.c_int32, []),
@@ -172,3 +173,14 @@ def lbm_last_error() -> str:
 
 def lbm_abi_version() -> int:
     return int(load().lbm_abi_version())
+
+
+def lbm_step_f64_noalloc(f_src_dev: int, f_dst_dev: int, adj_dev: int, n_fluid: int,
+                         omega_plus: float, omega_minus: float, force, alpha_dev,
+                         sums_dev: int, stream: int) -> None:
+    """One FP64 step on caller-owned arrays with no device allocation (for
+    callers that cannot allocate); see include/lbm.h."""
+    f = (ctypes.c_double * 3)(*[float(v) for v in force])
+    _check(load().lbm_step_f64_noalloc(f_src_dev, f_dst_dev, adj_dev, int(n_fluid),
+                                       float(omega_plus), float(omega_minus), f, alpha_dev,
+                                       sums_dev, stream))

@@ -25,6 +25,7 @@
 
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <thread>
 
 #include "lbm_internal.cuh"
@@ -630,4 +631,86 @@ extern "C" int lbm_synchronize(const lbm_state* st, double timeout_s) {
 
 extern "C" void lbm_set_timeout(double timeout_s) {
   if (timeout_s > 0) g_timeout_s = timeout_s;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free FP64 step.  The paper has no counterpart.  Some callers
+// cannot allocate device memory: a host application that owns all of the
+// GPU's memory and hands this library only the arrays it works on, or a
+// time-stepping loop with a fixed memory budget that cannot absorb the
+// device-wide synchronisation and latency of a cudaMalloc.  This entry point
+// takes every input and output from the caller and keeps its one piece of
+// scratch -- the FP64 block partial sums of the reduction -- in a fixed
+// static device array, present on every GPU that loads the library until
+// the process exits.
+namespace lbm {
+namespace {
+
+constexpr int64_t kStaticMaxBlocks = 65536;
+constexpr int64_t kStaticMaxCells = kStaticMaxBlocks * kSweepThreads;  // 16,777,216
+static __device__ __align__(256) double g_static_partials[kStaticMaxBlocks * 4];  // 2 MiB
+
+// Device address of g_static_partials on the current device, looked up once
+// per device (in host code the symbol is only a host-side stand-in).
+int static_partials(double** out) {
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static double* addr[kMaxDevices] = {};
+  int dev = 0;
+  LBM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(LBM_EINVAL, "device ordinal %d unsupported", dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    double* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_static_partials);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_static_partials)");
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return LBM_OK;
+}
+
+}  // namespace
+}  // namespace lbm
+
+extern "C" int lbm_step_f64_noalloc(const double* f_src_dev, double* f_dst_dev,
+                                    const int32_t* adj_dev, int64_t n_fluid, double omega_plus,
+                                    double omega_minus, const double force[3],
+                                    const double* alpha_dev, double* sums_dev, void* stream_v) {
+  clear_error();
+  if (n_fluid < 0 || n_fluid > kStaticMaxCells)
+    return fail(LBM_EINVAL,
+                "lbm_step_f64_noalloc handles at most %lld fluid cells (its static scratch "
+                "holds %lld block sums); got %lld",
+                (long long)kStaticMaxCells, (long long)kStaticMaxBlocks, (long long)n_fluid);
+  if (!sums_dev) return fail(LBM_EINVAL, "sums_dev is NULL");
+  if (n_fluid > 0 && (!f_src_dev || !f_dst_dev || !adj_dev))
+    return fail(LBM_EINVAL, "f_src_dev, f_dst_dev and adj_dev must be non-NULL");
+  if (n_fluid > 0 && f_src_dev == f_dst_dev)
+    return fail(LBM_EINVAL, "f_src_dev and f_dst_dev must be different arrays");
+  if (!(omega_plus > 0.0 && omega_plus < 2.0) || !(omega_minus > 0.0 && omega_minus < 2.0))
+    return fail(LBM_EINVAL, "relaxation rates must lie in (0, 2): %g, %g", omega_plus, omega_minus);
+  if (!force) return fail(LBM_EINVAL, "force is NULL");
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(force[d])) return fail(LBM_EINVAL, "force[%d] is not finite", d);
+  double* partials = nullptr;
+  int rc = static_partials(&partials);
+  if (rc != LBM_OK) return rc;
+  const cudaStream_t stream = (cudaStream_t)stream_v;
+  if (n_fluid == 0) {
+    LBM_CUDA_TRY(cudaMemsetAsync(sums_dev, 0, 4 * sizeof(double), stream));
+    return LBM_OK;
+  }
+  const int32_t n = (int32_t)n_fluid;
+  const int64_t nblocks = (n_fluid + kSweepThreads - 1) / kSweepThreads;
+  const Coef<double> k = make_coef<double>(omega_plus, omega_minus, force, 0);
+  if (alpha_dev)
+    sweep_kernel<LBM_F64, true, true><<<(unsigned)nblocks, kSweepThreads, 0, stream>>>(
+        f_src_dev, f_dst_dev, adj_dev, n, k, alpha_dev, partials);
+  else
+    sweep_kernel<LBM_F64, false, true><<<(unsigned)nblocks, kSweepThreads, 0, stream>>>(
+        f_src_dev, f_dst_dev, adj_dev, n, k, nullptr, partials);
+  final_sum_kernel<<<1, 1024, 0, stream>>>(partials, nblocks, sums_dev);
+  LBM_CUDA_TRY(cudaGetLastError());
+  return LBM_OK;
 }
