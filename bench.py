@@ -335,6 +335,55 @@ def _extras(lat, bed, wm, args):
     return out
 
 
+def run_precision_study(args):
+    """Storage forms against the FP64 GPU path on the 256x128x128 bed at
+    steady state (the FP64 path itself is held to the oracle within 1e-12 by
+    the parity tests): velocity-field L2 error, permeability (mean axial
+    velocity) error, mass drift and MFLUP/s.  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_1111_1129_gb300 import (LBMState, SparseLattice, capi, deviation_bound, inputs,
+                                       omega_minus, shifted_scale_exp)
+
+    capi.load()
+    wm = omega_minus(WP)
+    bed = inputs.bed_medium(0)
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), args.ordering, (8, 8, 8),
+                        bed.periodic)
+    k16 = shifted_scale_exp(deviation_bound(FORCE[0], 61.0, WP))
+    rows = {}
+    ref_u = ref_flux = None
+    for prec in ("f64", "f32s", "f16s", "f32", "bf16s"):
+        st = LBMState(lat, prec, k16)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st.step(args.study_steps, WP, wm, FORCE)
+        e1.record()
+        mass, flux = st.reduce_flux(AXIS)
+        ms = e0.elapsed_time(e1)
+        _, u = st.moments()
+        u = u.cpu().numpy()
+        st.close()
+        if ref_u is None:
+            ref_u, ref_flux = u, flux
+        rows[prec] = {
+            "mflups": lat.n * args.study_steps / (ms * 1e-3) / 1e6,
+            "u_l2_rel_vs_f64": float(np.linalg.norm(u - ref_u) / np.linalg.norm(ref_u)),
+            "permeability_rel_vs_f64": abs(flux - ref_flux) / abs(ref_flux),
+            "mass_drift_rel": abs(mass - lat.n) / lat.n,
+            "finite": bool(np.isfinite(u).all()),
+        }
+    line = {"study": "storage precision at steady state",
+            "workload": WORKLOADS["medium"][0], "fluid_cells": lat.n,
+            "steps": args.study_steps, "force": list(FORCE), "ordering": args.ordering,
+            "scale_exp_16bit": k16, "reference": "f64 GPU path", "forms": rows}
+    lat.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,9 +398,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="run the storage-precision study instead of the benchmark")
+    ap.add_argument("--study-steps", type=int, default=20000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.precision_study:
+        return run_precision_study(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

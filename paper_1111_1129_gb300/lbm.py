@@ -27,6 +27,30 @@ def omega_minus(omega_plus: float, magic: float = 3.0 / 16.0) -> float:
     return 1.0 / (0.5 + magic / (1.0 / omega_plus - 0.5))
 
 
+def deviation_bound(force: float, tube_radius: float, omega_plus: float) -> float:
+    """Upper estimate of |f_q - w_q| for a body-force-driven flow in a tube.
+
+    The fastest flow the force can drive through a tube of this radius is
+    the empty tube's Hagen-Poiseuille centreline speed u = F R^2 / (4 nu);
+    packing only slows it.  The largest equilibrium deviation is then about
+    w_q 3 |c.u| <= u / 6 (axis and diagonal links alike); a factor 2 covers
+    density and non-equilibrium parts."""
+    nu = (1.0 / omega_plus - 0.5) / 3.0
+    u = abs(force) * tube_radius * tube_radius / (4.0 * nu)
+    return 2.0 * u / 6.0
+
+
+def shifted_scale_exp(dev_bound: float, target_log2: int = 14) -> int:
+    """Scale exponent k of the 16-bit shifted forms: the largest expected
+    deviation times 2^k lands at 2^target_log2, below FP16's largest finite
+    value (65504 ~ 2^16) with 4x headroom.  Because FP16 and BF16 are
+    floating point, a k that is a few powers of two too small costs no
+    precision; only overflow (k far too large) would."""
+    if dev_bound <= 0:
+        return 0
+    return int(max(0, min(40, math.floor(target_log2 - math.log2(dev_bound)))))
+
+
 class _DeviceView:
     """Borrowed device buffer exposed through __cuda_array_interface__."""
 
