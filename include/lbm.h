@@ -230,8 +230,44 @@ int lbm_step_f64_noalloc(const double* f_src_dev, double* f_dst_dev, const int32
                          const double force[3], const double* alpha_dev, double* sums_dev,
                          void* stream);
 
-/* Release a handle returned by this library (sparse or state); NULL is a
- * no-op.  Waits for the handle's stream before freeing. */
+/* ---- adjoint (reverse mode) ---------------------------------------------
+ * Gradients of J = (1/N) sum_n u_axis,n, the mean axial velocity of the
+ * collision of step K, with respect to the body force F and the per-cell
+ * Brinkman damping alpha_n, for K steps started from a state's current
+ * PDFs: lam_g_K = dJ/dg_K; lam_f_{t-1} = S^T lam_g_t (transposed pull);
+ * lam_g_t = C'(g_t)^T lam_f_t (transposed TRT Jacobian).  The forward
+ * states are kept as checkpoints every `stride` steps in the state's
+ * storage form and recomputed between checkpoints (memory ~ (K/stride +
+ * stride) states).  Adjoint arithmetic runs in the state's arithmetic
+ * precision (FP64 for LBM_F64, FP32 otherwise); sums in FP64.
+ */
+typedef struct lbm_adjoint lbm_adjoint;
+
+/* Buffers for K = n_steps >= 1 steps of state st (its lattice, form and
+ * damping); stride = 0 picks ceil(sqrt(K)).  The state must outlive it. */
+int lbm_adjoint_create(const lbm_state* st, int32_t n_steps, int32_t stride, lbm_adjoint** out);
+
+/* Forward pass from the state's current PDFs (the state is not modified):
+ * stores the checkpoints and returns J (axis in {0,1,2}).  Synchronises. */
+int lbm_adjoint_forward(lbm_adjoint* adj, double omega_plus, double omega_minus,
+                        const double force[3], int32_t axis, double* J_out);
+
+/* Reverse pass of the last lbm_adjoint_forward.  dJdF_out: host double[3].
+ * dJdalpha_dev: device FP64[N] (fluid order), written, or NULL.
+ * dJdf0_dev: device FP64[19*N], gradient with respect to the initial PDFs,
+ * written, or NULL.  May be called again (it recomputes from the
+ * checkpoints).  Synchronises. */
+int lbm_adjoint_backward(lbm_adjoint* adj, double dJdF_out[3], double* dJdalpha_dev,
+                         double* dJdf0_dev);
+
+/* Forward and reverse pass in one call; n_steps must equal the K the
+ * adjoint was created for and st its state. */
+int lbm_adjoint_step(lbm_state* st, lbm_adjoint* adj, int32_t n_steps, double omega_plus,
+                     double omega_minus, const double force[3], int32_t axis, double* J_out,
+                     double dJdF_out[3], double* dJdalpha_dev);
+
+/* Release a handle returned by this library (sparse, state or adjoint);
+ * NULL is a no-op.  Waits for the handle's stream before freeing. */
 void lbm_free(void* handle);
 
 /* Description of the last failure on this thread ("" if none). */

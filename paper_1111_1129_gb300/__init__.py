@@ -9,8 +9,8 @@ loads nothing; the library is loaded on first use and its absence is an
 error, never a fallback.
 """
 
-__all__ = ["SparseLattice", "LBMState", "omega_minus", "ordering_keys", "deviation_bound",
-           "shifted_scale_exp"]
+__all__ = ["SparseLattice", "LBMState", "Adjoint", "LBMFlux", "omega_minus", "ordering_keys",
+           "deviation_bound", "shifted_scale_exp"]
 
 
 def __getattr__(name):

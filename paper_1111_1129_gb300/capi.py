@@ -44,6 +44,10 @@ SIGNATURES = {
     "lbm_synchronize": (ctypes.c_int, [_vp, _d]),
     "lbm_set_timeout": (None, [_d]),
     "lbm_step_f64_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i64, _d, _d, _vp, _vp, _vp, _vp]),
+    "lbm_adjoint_create": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
+    "lbm_adjoint_forward": (ctypes.c_int, [_vp, _d, _d, _vp, _i32, _vp]),
+    "lbm_adjoint_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_adjoint_step": (ctypes.c_int, [_vp, _vp, _i32, _d, _d, _vp, _i32, _vp, _vp, _vp]),
     "lbm_free": (None, [_vp]),
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_abi_version": (ctypes.c_int32, []),
@@ -160,6 +164,40 @@ def lbm_synchronize(state: int, timeout_s: float = 0.0) -> None:
 
 def lbm_set_timeout(timeout_s: float) -> None:
     load().lbm_set_timeout(float(timeout_s))
+
+
+def lbm_adjoint_create(state: int, n_steps: int, stride: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _check(load().lbm_adjoint_create(state, int(n_steps), int(stride), ctypes.byref(out)))
+    return out.value
+
+
+def lbm_adjoint_forward(adjoint: int, omega_plus: float, omega_minus: float, force,
+                        axis: int) -> float:
+    f = (ctypes.c_double * 3)(*[float(v) for v in force])
+    J = ctypes.c_double()
+    _check(load().lbm_adjoint_forward(adjoint, float(omega_plus), float(omega_minus), f,
+                                      int(axis), ctypes.byref(J)))
+    return J.value
+
+
+def lbm_adjoint_backward(adjoint: int, dJdalpha_dev=None, dJdf0_dev=None):
+    """dJ/dF as a tuple; fills the optional device outputs."""
+    dF = (ctypes.c_double * 3)()
+    _check(load().lbm_adjoint_backward(adjoint, dF, dJdalpha_dev, dJdf0_dev))
+    return tuple(dF)
+
+
+def lbm_adjoint_step(state: int, adjoint: int, n_steps: int, omega_plus: float,
+                     omega_minus: float, force, axis: int, dJdalpha_dev=None):
+    """(J, dJ/dF) of one forward + reverse pass."""
+    f = (ctypes.c_double * 3)(*[float(v) for v in force])
+    J = ctypes.c_double()
+    dF = (ctypes.c_double * 3)()
+    _check(load().lbm_adjoint_step(state, adjoint, int(n_steps), float(omega_plus),
+                                   float(omega_minus), f, int(axis), ctypes.byref(J), dF,
+                                   dJdalpha_dev))
+    return J.value, tuple(dF)
 
 
 def lbm_free(handle) -> None:

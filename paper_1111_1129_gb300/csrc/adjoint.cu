@@ -1,0 +1,513 @@
+// Reverse mode (adjoint) of the sweep, for gradients of the mean axial
+// velocity J = (1/N) sum_n u_axis,n of the collision of step K with respect
+// to the body force F and a per-cell Brinkman damping alpha_n.
+//
+// Forward: f_0 given; for t = 1..K: g_t = S f_{t-1} (pull through the
+// adjacency list), f_t = C(g_t; F, alpha) (TRT collision).  Reverse:
+//   lam_g_K = dJ/dg_K,  lam_f_{t-1} = S^T lam_g_t,
+//   lam_g_t = C'(g_t)^T lam_f_t  (t = K-1 .. 1),
+// with dJ/dF and dJ/dalpha accumulated from every step.
+//
+// S^T needs no second index array: slot (q, m) is read in the forward pull
+// either by the downstream cell k = m + c_q in direction q, whose
+// adj[q-1][k] = q N + m, or -- when m + c_q is solid or beyond a closed
+// face -- by m itself in direction opp(q) (bounce back).  Both cases are
+// visible in adj[opp(q)-1][m], the pull of direction opp(q) at m, whose
+// source is exactly m + c_q.
+//
+// C'^T is applied in closed form.  Writing the collision as
+//   f*_q = L(g)_q + E_q(rho, u) + S_q(u),
+//   L(g)_q = (1 - (w+ + w-)/2) g_q + ((w- - w+)/2) g_opp(q),
+//   E_q = w+ w_q (rho + 4.5 (c_q.u)^2 - 1.5 u.u) + 3 w- w_q c_q.u,
+//   S_q = (1 - w-/2) 3 w_q c_q.(F - alpha u),
+// with drho/dg_r = 1 and du/dg_r = s c_r (s = 1/(1 + alpha/2)), one gets
+//   lam_g_r = L^T(lam)_r + w+ M0 + s c_r.G,
+//   G = 9 w+ M2 u - 3 w+ M0 u + 3 (w- - alpha (1 - w-/2)) M1,
+//   dJ/dF     += (s/2) G + 3 (1 - w-/2) M1,
+//   dJ/dalpha += -(s/2) G.u - 3 (1 - w-/2) M1.u,
+// where M0 = sum w_q lam_q, M1 = sum w_q lam_q c_q, M2 = sum w_q lam_q c_q c_q^T.
+//
+// Memory: checkpoints of f every `stride` steps (stride ~ sqrt(K)) in the
+// state's storage form, one segment of `stride` recomputed states, two
+// adjoint buffers in the arithmetic precision.
+#include <cmath>
+
+#include "lbm_kernels.cuh"
+
+struct lbm_adjoint {
+  uint32_t magic;
+  const lbm_state* st;
+  int32_t K, stride, n_ckpt;
+  void* ckpt;       // n_ckpt states of 19 N storage elements
+  void* seg;        // max(stride, 2) states
+  void* lam[2];     // 19 N arithmetic-precision adjoints
+  double* part;     // [nblocks][4]: dJ/dF_x, dJ/dF_y, dJ/dF_z, sum u_axis
+  double* dalpha;   // [N]
+  double* red_dev;  // [4]
+  double* red_host; // [4], pinned
+  cudaEvent_t done;
+  int have_forward;
+  double wp, wm, F[3];
+  int32_t axis;
+};
+
+namespace lbm {
+namespace {
+
+template <class C>
+struct AdjCoef {
+  C wp, one_m_wp;  // w+, 1 - w+
+  C k1, k2;        // 1 - (w+ + w-)/2, (w- - w+)/2
+  C wm, src;       // w-, 1 - w-/2
+  C inv_n;         // 1 / N
+};
+
+template <class C>
+AdjCoef<C> make_adj_coef(double wp, double wm, int64_t n) {
+  AdjCoef<C> a;
+  a.wp = (C)wp;
+  a.one_m_wp = (C)(1.0 - wp);
+  a.k1 = (C)(1.0 - 0.5 * (wp + wm));
+  a.k2 = (C)(0.5 * (wm - wp));
+  a.wm = (C)wm;
+  a.src = (C)(1.0 - 0.5 * wm);
+  a.inv_n = (C)(n > 0 ? 1.0 / (double)n : 0.0);
+  return a;
+}
+
+// Flat slot, in the adjoint of the pulled values, that holds the adjoint of
+// stored slot (q, i): s = adj[opp(q)-1][i].
+__device__ __forceinline__ int32_t reverse_slot(int q, int32_t s, int32_t n, int32_t i) {
+  const int o = opp(q);
+  return s == q * n + i ? o * n + i : s + (q - o) * n;
+}
+
+// Velocity of the collision of the pulled values g (same arithmetic as the
+// collision) and s = 1 / (1 + alpha/2).
+template <class C, bool DAMPED>
+__device__ __forceinline__ void velocity(const C g[19], const Coef<C>& k, C alpha, C u[3], C& s) {
+  C d[9];
+#pragma unroll
+  for (int p = 0; p < 9; ++p) d[p] = g[2 * p + 1] - g[2 * p + 2];
+  const C jx = ((d[0] + d[3]) + (d[4] + d[5])) + d[6];
+  const C jy = ((d[1] + d[3]) - (d[4] - d[7])) + d[8];
+  const C jz = ((d[2] + d[5]) - (d[6] - d[7])) - d[8];
+  s = DAMPED ? C(1) / (C(1) + C(0.5) * alpha) : C(1);
+  u[0] = (jx + k.hF[0]) * s;
+  u[1] = (jy + k.hF[1]) * s;
+  u[2] = (jz + k.hF[2]) * s;
+}
+
+__device__ __forceinline__ int axis_component(int q, int axis) {
+  return axis == 0 ? cx(q) : (axis == 1 ? cy(q) : cz(q));
+}
+
+// Block-sum 4 doubles and add them to acc[4] (each block owns its slot;
+// launches on one stream are ordered, so the accumulation is race free).
+__device__ __forceinline__ void block_accumulate4(double v[4], double* acc, bool assign) {
+  __shared__ double sm[kSweepThreads / 32][4];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sm[warp][j] = v[j];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kSweepThreads / 32; ++w) s += sm[w][threadIdx.x];
+    acc[threadIdx.x] = assign ? s : acc[threadIdx.x] + s;
+  }
+}
+
+// Seed: lam_g_K = dJ/dg_K from f_{K-1}; initialises dJ/dF, dJ/dalpha and
+// the sum of u_axis (J = sum / N).
+template <int PREC, bool DAMPED>
+__global__ void __launch_bounds__(kSweepThreads)
+    adjoint_seed_kernel(const typename Form<PREC>::S* __restrict__ f_prev,
+                        const int32_t* __restrict__ adj, int32_t n,
+                        Coef<typename Form<PREC>::C> k, AdjCoef<typename Form<PREC>::C> a,
+                        const typename Form<PREC>::C* __restrict__ alpha, int axis,
+                        typename Form<PREC>::C* __restrict__ lam_out, double* __restrict__ part,
+                        double* __restrict__ dalpha) {
+  using C = typename Form<PREC>::C;
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < n) {
+    C g[19];
+    gather<PREC>(f_prev, adj, n, i, k.inv_scale, g);
+    C u[3], s;
+    const C al = DAMPED ? alpha[i] : C(0);
+    velocity<C, DAMPED>(g, k, al, u, s);
+    const C seed = s * a.inv_n;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) lam_out[q * n + i] = C(axis_component(q, axis)) * seed;
+    red[axis] = 0.5 * (double)seed;
+    red[3] = (double)u[axis];
+    dalpha[i] = -0.5 * (double)seed * (double)u[axis];
+  }
+  block_accumulate4(red, part + 4 * (int64_t)blockIdx.x, true);
+}
+
+// One reverse step t: lam_f_t = S^T lam_g_{t+1} (gathered), then
+// lam_g_t = C'(g_t)^T lam_f_t with g_t pulled from f_{t-1}.
+template <int PREC, bool DAMPED>
+__global__ void __launch_bounds__(kSweepThreads)
+    adjoint_step_kernel(const typename Form<PREC>::S* __restrict__ f_prev,
+                        const int32_t* __restrict__ adj, int32_t n,
+                        Coef<typename Form<PREC>::C> k, AdjCoef<typename Form<PREC>::C> a,
+                        const typename Form<PREC>::C* __restrict__ alpha,
+                        const typename Form<PREC>::C* __restrict__ lam_in,
+                        typename Form<PREC>::C* __restrict__ lam_out, double* __restrict__ part,
+                        double* __restrict__ dalpha) {
+  using C = typename Form<PREC>::C;
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < n) {
+    int32_t idx[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) idx[q] = __ldg(adj + q * n + i);
+    C lf[19], g[19];
+    lf[0] = lam_in[i];
+    g[0] = decode<PREC>(load_ro<PREC>(f_prev + i), k.inv_scale);
+#pragma unroll
+    for (int q = 1; q < 19; ++q) {
+      lf[q] = lam_in[reverse_slot(q, idx[opp(q) - 1], n, i)];
+      g[q] = decode<PREC>(load_ro<PREC>(f_prev + idx[q - 1]), k.inv_scale);
+    }
+    C u[3], s;
+    const C al = DAMPED ? alpha[i] : C(0);
+    velocity<C, DAMPED>(g, k, al, u, s);
+    // weighted moments of the adjoint
+    C S[9], D[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      S[p] = lf[2 * p + 1] + lf[2 * p + 2];
+      D[p] = lf[2 * p + 1] - lf[2 * p + 2];
+    }
+    const C w0 = C(1.0 / 3.0), w1 = C(1.0 / 18.0), w2 = C(1.0 / 36.0);
+    const C M0 = w0 * lf[0] + w1 * (S[0] + S[1] + S[2]) +
+                 w2 * (((S[3] + S[4]) + (S[5] + S[6])) + (S[7] + S[8]));
+    const C M1x = w1 * D[0] + w2 * ((D[3] + D[4]) + (D[5] + D[6]));
+    const C M1y = w1 * D[1] + w2 * ((D[3] - D[4]) + (D[7] + D[8]));
+    const C M1z = w1 * D[2] + w2 * ((D[5] - D[6]) + (D[7] - D[8]));
+    const C Mxx = w1 * S[0] + w2 * ((S[3] + S[4]) + (S[5] + S[6]));
+    const C Myy = w1 * S[1] + w2 * ((S[3] + S[4]) + (S[7] + S[8]));
+    const C Mzz = w1 * S[2] + w2 * ((S[5] + S[6]) + (S[7] + S[8]));
+    const C Mxy = w2 * (S[3] - S[4]);
+    const C Mxz = w2 * (S[5] - S[6]);
+    const C Myz = w2 * (S[7] - S[8]);
+    const C nine_wp = C(9) * a.wp, three_wp_m0 = C(3) * a.wp * M0;
+    const C beta = C(3) * (a.wm - al * a.src);
+    const C Gx = nine_wp * (Mxx * u[0] + Mxy * u[1] + Mxz * u[2]) - three_wp_m0 * u[0] + beta * M1x;
+    const C Gy = nine_wp * (Mxy * u[0] + Myy * u[1] + Myz * u[2]) - three_wp_m0 * u[1] + beta * M1y;
+    const C Gz = nine_wp * (Mxz * u[0] + Myz * u[1] + Mzz * u[2]) - three_wp_m0 * u[2] + beta * M1z;
+    const C base = a.wp * M0;
+    lam_out[i] = a.one_m_wp * lf[0] + base;
+#define LBM_ADJ_PAIR(P, CG)                                                    \
+  {                                                                            \
+    const C sg_ = s * (CG);                                                    \
+    lam_out[(2 * P + 1) * n + i] = a.k1 * lf[2 * P + 1] + a.k2 * lf[2 * P + 2] + base + sg_; \
+    lam_out[(2 * P + 2) * n + i] = a.k1 * lf[2 * P + 2] + a.k2 * lf[2 * P + 1] + base - sg_; \
+  }
+    LBM_ADJ_PAIR(0, Gx)
+    LBM_ADJ_PAIR(1, Gy)
+    LBM_ADJ_PAIR(2, Gz)
+    LBM_ADJ_PAIR(3, Gx + Gy)
+    LBM_ADJ_PAIR(4, Gx - Gy)
+    LBM_ADJ_PAIR(5, Gx + Gz)
+    LBM_ADJ_PAIR(6, Gx - Gz)
+    LBM_ADJ_PAIR(7, Gy + Gz)
+    LBM_ADJ_PAIR(8, Gy - Gz)
+#undef LBM_ADJ_PAIR
+    const C hs = C(0.5) * s, three_src = C(3) * a.src;
+    red[0] = (double)(hs * Gx + three_src * M1x);
+    red[1] = (double)(hs * Gy + three_src * M1y);
+    red[2] = (double)(hs * Gz + three_src * M1z);
+    const C Gu = Gx * u[0] + Gy * u[1] + Gz * u[2];
+    const C M1u = M1x * u[0] + M1y * u[1] + M1z * u[2];
+    dalpha[i] += (double)(-hs * Gu - three_src * M1u);
+  }
+  block_accumulate4(red, part + 4 * (int64_t)blockIdx.x, false);
+}
+
+// lam_f_0 = S^T lam_g_1 (gradient with respect to the initial PDFs).
+template <class C>
+__global__ void __launch_bounds__(kSweepThreads)
+    adjoint_initial_kernel(const int32_t* __restrict__ adj, int32_t n,
+                           const C* __restrict__ lam_in, double* __restrict__ out) {
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  if (i >= n) return;
+  out[i] = (double)lam_in[i];
+#pragma unroll
+  for (int q = 1; q < 19; ++q)
+    out[q * n + i] = (double)lam_in[reverse_slot(q, adj[(opp(q) - 1) * n + i], n, i)];
+}
+
+// ---- host orchestration -------------------------------------------------------
+
+template <int PREC>
+struct Runner {
+  using S = typename Form<PREC>::S;
+  using C = typename Form<PREC>::C;
+  lbm_adjoint* ad;
+  const lbm_state* st;
+  int32_t n;
+  cudaStream_t stream;
+  unsigned grid;
+  Coef<C> k;
+  AdjCoef<C> a;
+  const C* alpha;
+  size_t state_elems;
+
+  Runner(lbm_adjoint* ad_) : ad(ad_), st(ad_->st) {
+    n = (int32_t)st->sp->n;
+    stream = st->sp->stream;
+    grid = (unsigned)st->nblocks;
+    k = make_coef<C>(ad->wp, ad->wm, ad->F, st->scale_exp);
+    a = make_adj_coef<C>(ad->wp, ad->wm, n);
+    alpha = (const C*)st->alpha;
+    state_elems = 19 * (size_t)n;
+  }
+  S* ckpt(int j) const { return (S*)ad->ckpt + (size_t)j * state_elems; }
+  S* seg(int i) const { return (S*)ad->seg + (size_t)i * state_elems; }
+  C* lam(int i) const { return (C*)ad->lam[i]; }
+
+  void step(const S* src, S* dst) const {
+    if (alpha)
+      sweep_kernel<PREC, true, false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, nullptr);
+    else
+      sweep_kernel<PREC, false, false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, nullptr);
+  }
+  void seed(const S* f_prev) const {
+    if (alpha)
+      adjoint_seed_kernel<PREC, true><<<grid, kSweepThreads, 0, stream>>>(f_prev, st->sp->adj, n, k, a, alpha, ad->axis, lam(0), ad->part, ad->dalpha);
+    else
+      adjoint_seed_kernel<PREC, false><<<grid, kSweepThreads, 0, stream>>>(f_prev, st->sp->adj, n, k, a, alpha, ad->axis, lam(0), ad->part, ad->dalpha);
+  }
+  void reverse(const S* f_prev, int in) const {
+    if (alpha)
+      adjoint_step_kernel<PREC, true><<<grid, kSweepThreads, 0, stream>>>(f_prev, st->sp->adj, n, k, a, alpha, lam(in), lam(in ^ 1), ad->part, ad->dalpha);
+    else
+      adjoint_step_kernel<PREC, false><<<grid, kSweepThreads, 0, stream>>>(f_prev, st->sp->adj, n, k, a, alpha, lam(in), lam(in ^ 1), ad->part, ad->dalpha);
+  }
+
+  // Forward pass from the state's current PDFs: checkpoints f_{j*stride};
+  // *last receives where f_{K-1} is.
+  int forward(const S** last) const {
+    LBM_CUDA_TRY(cudaMemcpyAsync(ckpt(0), st->buf[st->cur], state_elems * sizeof(S),
+                                 cudaMemcpyDeviceToDevice, stream));
+    const S* cur = ckpt(0);
+    for (int32_t t = 1; t <= ad->K - 1; ++t) {
+      S* dst = (t % ad->stride == 0) ? ckpt(t / ad->stride) : seg(t & 1);
+      step(cur, dst);
+      cur = dst;
+    }
+    *last = cur;
+    return LBM_OK;
+  }
+
+  // Recompute segment j: f_{j*stride + i} for i = 0..last into seg slots
+  // (slot 0 is the checkpoint itself).
+  void recompute(int j, int last) const {
+    const S* cur = ckpt(j);
+    for (int i = 1; i <= last; ++i) {
+      step(cur, seg(i));
+      cur = seg(i);
+    }
+  }
+  const S* state_at(int j, int i) const { return i == 0 ? ckpt(j) : seg(i); }
+
+  int backward(double* dJdf0) const {
+    const int K = ad->K, s = ad->stride;
+    int j = (K - 1) / s;
+    recompute(j, (K - 1) - j * s);
+    seed(state_at(j, (K - 1) - j * s));
+    int in = 0;
+    for (int t = K - 1; t >= 1; --t) {
+      const int jj = (t - 1) / s;
+      if (jj != j) {
+        j = jj;
+        recompute(j, s - 1);
+      }
+      reverse(state_at(j, (t - 1) - j * s), in);
+      in ^= 1;
+    }
+    if (dJdf0)
+      adjoint_initial_kernel<C><<<grid, kSweepThreads, 0, stream>>>(st->sp->adj, n, lam(in), dJdf0);
+    LBM_CUDA_TRY(cudaGetLastError());
+    return LBM_OK;
+  }
+};
+
+template <int PREC>
+int run_forward(lbm_adjoint* ad) {
+  Runner<PREC> r(ad);
+  if (r.n == 0) return LBM_OK;
+  const typename Runner<PREC>::S* last = nullptr;
+  const int rc = r.forward(&last);
+  if (rc != LBM_OK) return rc;
+  r.seed(last);
+  LBM_CUDA_TRY(cudaGetLastError());
+  return LBM_OK;
+}
+
+template <int PREC>
+int run_backward(lbm_adjoint* ad, double* dJdf0) {
+  Runner<PREC> r(ad);
+  if (r.n == 0) return LBM_OK;
+  return r.backward(dJdf0);
+}
+
+#define LBM_ADJ_DISPATCH(prec, fn, ...)                      \
+  switch (prec) {                                            \
+    case LBM_F64: return fn<LBM_F64>(__VA_ARGS__);           \
+    case LBM_F32: return fn<LBM_F32>(__VA_ARGS__);           \
+    case LBM_F32S: return fn<LBM_F32S>(__VA_ARGS__);         \
+    case LBM_F16S: return fn<LBM_F16S>(__VA_ARGS__);         \
+    default: return fn<LBM_BF16S>(__VA_ARGS__);              \
+  }
+
+int dispatch_forward(lbm_adjoint* ad) { LBM_ADJ_DISPATCH(ad->st->precision, run_forward, ad) }
+int dispatch_backward(lbm_adjoint* ad, double* dJdf0) {
+  LBM_ADJ_DISPATCH(ad->st->precision, run_backward, ad, dJdf0)
+}
+
+bool valid_adjoint(const lbm_adjoint* ad) { return ad && ad->magic == kMagicAdjoint; }
+
+// Final sums of the per-block accumulators into red_host.
+int finish_sums(lbm_adjoint* ad) {
+  const cudaStream_t stream = ad->st->sp->stream;
+  if (ad->st->sp->n == 0) {
+    for (int j = 0; j < 4; ++j) ad->red_host[j] = 0.0;
+    return LBM_OK;
+  }
+  final_sum_kernel<<<1, 1024, 0, stream>>>(ad->part, ad->st->nblocks, ad->red_dev);
+  LBM_CUDA_TRY(cudaGetLastError());
+  LBM_CUDA_TRY(cudaMemcpyAsync(ad->red_host, ad->red_dev, 4 * sizeof(double),
+                               cudaMemcpyDeviceToHost, stream));
+  return wait_event(ad->done, stream, 0.0);
+}
+
+}  // namespace
+
+void free_adjoint(lbm_adjoint* ad) {
+  if (!ad) return;
+  cudaStreamSynchronize(ad->st ? ad->st->sp->stream : nullptr);
+  for (void* p : {ad->ckpt, ad->seg, ad->lam[0], ad->lam[1], (void*)ad->part,
+                  (void*)ad->dalpha, (void*)ad->red_dev})
+    if (p) cudaFree(p);
+  if (ad->red_host) cudaFreeHost(ad->red_host);
+  if (ad->done) cudaEventDestroy(ad->done);
+  ad->magic = 0;
+  delete ad;
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+extern "C" int lbm_adjoint_create(const lbm_state* st, int32_t n_steps, int32_t stride,
+                                  lbm_adjoint** out) {
+  clear_error();
+  if (!out) return fail(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  if (n_steps < 1) return fail(LBM_EINVAL, "n_steps = %d must be >= 1", n_steps);
+  if (stride < 0) return fail(LBM_EINVAL, "checkpoint stride %d < 0", stride);
+  if (stride == 0) stride = (int32_t)std::ceil(std::sqrt((double)n_steps));
+  if (stride > n_steps) stride = n_steps;
+  lbm_adjoint* ad = new lbm_adjoint{};
+  ad->magic = kMagicAdjoint;
+  ad->st = st;
+  ad->K = n_steps;
+  ad->stride = stride;
+  ad->n_ckpt = (n_steps - 1) / stride + 1;
+  const size_t n = (size_t)(st->sp->n > 0 ? st->sp->n : 1);
+  const size_t sbytes = storage_bytes(st->precision) * 19 * n;
+  const size_t cbytes = compute_bytes(st->precision) * 19 * n;
+  const int nseg = stride > 2 ? stride : 2;
+  bool ok = cudaMalloc(&ad->ckpt, sbytes * ad->n_ckpt) == cudaSuccess &&
+            cudaMalloc(&ad->seg, sbytes * nseg) == cudaSuccess &&
+            cudaMalloc(&ad->lam[0], cbytes) == cudaSuccess &&
+            cudaMalloc(&ad->lam[1], cbytes) == cudaSuccess &&
+            cudaMalloc(&ad->part, sizeof(double) * 4 * st->nblocks) == cudaSuccess &&
+            cudaMalloc(&ad->dalpha, sizeof(double) * n) == cudaSuccess &&
+            cudaMalloc(&ad->red_dev, sizeof(double) * 4) == cudaSuccess &&
+            cudaMallocHost(&ad->red_host, sizeof(double) * 4) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ad->done, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_adjoint(ad);
+    return fail(LBM_ENOMEM, "adjoint allocation failed (%d checkpoints + %d segment states of %zu bytes)",
+                (int)((n_steps - 1) / stride + 1), nseg, sbytes);
+  }
+  *out = ad;
+  return LBM_OK;
+}
+
+extern "C" int lbm_adjoint_forward(lbm_adjoint* ad, double omega_plus, double omega_minus,
+                                   const double force[3], int32_t axis, double* J_out) {
+  clear_error();
+  if (!valid_adjoint(ad)) return fail(LBM_EINVAL, "not an adjoint handle");
+  if (!valid_state(ad->st)) return fail(LBM_EINVAL, "the adjoint's state was released");
+  if (axis < 0 || axis > 2) return fail(LBM_EINVAL, "axis %d outside {0,1,2}", axis);
+  if (!(omega_plus > 0.0 && omega_plus < 2.0) || !(omega_minus > 0.0 && omega_minus < 2.0))
+    return fail(LBM_EINVAL, "relaxation rates must lie in (0, 2): %g, %g", omega_plus, omega_minus);
+  if (!force) return fail(LBM_EINVAL, "force is NULL");
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(force[d])) return fail(LBM_EINVAL, "force[%d] is not finite", d);
+  ad->wp = omega_plus;
+  ad->wm = omega_minus;
+  for (int d = 0; d < 3; ++d) ad->F[d] = force[d];
+  ad->axis = axis;
+  int rc = dispatch_forward(ad);
+  if (rc != LBM_OK) return rc;
+  rc = finish_sums(ad);
+  if (rc != LBM_OK) return rc;
+  const int64_t n = ad->st->sp->n;
+  const double J = n > 0 ? ad->red_host[3] / (double)n : 0.0;
+  if (!std::isfinite(J)) return fail(LBM_ENONFINITE, "objective is not finite");
+  ad->have_forward = 1;
+  if (J_out) *J_out = J;
+  return LBM_OK;
+}
+
+extern "C" int lbm_adjoint_backward(lbm_adjoint* ad, double dJdF_out[3], double* dJdalpha_dev,
+                                    double* dJdf0_dev) {
+  clear_error();
+  if (!valid_adjoint(ad)) return fail(LBM_EINVAL, "not an adjoint handle");
+  if (!valid_state(ad->st)) return fail(LBM_EINVAL, "the adjoint's state was released");
+  if (!ad->have_forward) return fail(LBM_EINVAL, "lbm_adjoint_forward has not run");
+  int rc = dispatch_backward(ad, dJdf0_dev);
+  if (rc != LBM_OK) return rc;
+  const cudaStream_t stream = ad->st->sp->stream;
+  const int64_t n = ad->st->sp->n;
+  if (dJdalpha_dev && n > 0)
+    LBM_CUDA_TRY(cudaMemcpyAsync(dJdalpha_dev, ad->dalpha, sizeof(double) * n,
+                                 cudaMemcpyDeviceToDevice, stream));
+  rc = finish_sums(ad);
+  if (rc != LBM_OK) return rc;
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(ad->red_host[d])) return fail(LBM_ENONFINITE, "dJ/dF is not finite");
+  if (dJdF_out)
+    for (int d = 0; d < 3; ++d) dJdF_out[d] = ad->red_host[d];
+  return LBM_OK;
+}
+
+extern "C" int lbm_adjoint_step(lbm_state* st, lbm_adjoint* ad, int32_t n_steps,
+                                double omega_plus, double omega_minus, const double force[3],
+                                int32_t axis, double* J_out, double dJdF_out[3],
+                                double* dJdalpha_dev) {
+  clear_error();
+  if (!valid_adjoint(ad)) return fail(LBM_EINVAL, "not an adjoint handle");
+  if (ad->st != st) return fail(LBM_EINVAL, "the adjoint was created for another state");
+  if (n_steps != ad->K)
+    return fail(LBM_EINVAL, "the adjoint was created for %d steps, not %d", ad->K, n_steps);
+  int rc = lbm_adjoint_forward(ad, omega_plus, omega_minus, force, axis, J_out);
+  if (rc != LBM_OK) return rc;
+  return lbm_adjoint_backward(ad, dJdF_out, dJdalpha_dev, nullptr);
+}

@@ -45,6 +45,7 @@ extern "C" void lbm_free(void* handle) {
   const uint32_t magic = *static_cast<const uint32_t*>(handle);
   if (magic == lbm::kMagicSparse) lbm::free_sparse(static_cast<lbm_sparse*>(handle));
   else if (magic == lbm::kMagicState) lbm::free_state(static_cast<lbm_state*>(handle));
+  else if (magic == lbm::kMagicAdjoint) lbm::free_adjoint(static_cast<lbm_adjoint*>(handle));
 }
 
 extern "C" const char* lbm_last_error(void) { return lbm::g_last_error.c_str(); }

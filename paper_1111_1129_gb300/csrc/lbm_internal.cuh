@@ -10,6 +10,7 @@ namespace lbm {
 
 constexpr uint32_t kMagicSparse = 0x4C53504Bu;
 constexpr uint32_t kMagicState = 0x4C535354u;
+constexpr uint32_t kMagicAdjoint = 0x4C53414Du;
 constexpr int kSweepThreads = 256;
 
 // Records a message for lbm_last_error() and returns `status`.
@@ -177,4 +178,11 @@ struct lbm_state {
 namespace lbm {
 void free_state(lbm_state* st);
 void free_sparse(lbm_sparse* sp);
+void free_adjoint(lbm_adjoint* ad);
+size_t storage_bytes(int prec);   // bytes per stored PDF of a precision form
+size_t compute_bytes(int prec);   // bytes of the arithmetic type of a form
+bool valid_state(const lbm_state* st);
+// Records `ev` on `stream` and polls it with a wall-clock limit (<= 0: the
+// library default); LBM_ETIMEOUT if the work is still running then.
+int wait_event(cudaEvent_t ev, cudaStream_t stream, double timeout_s);
 }  // namespace lbm

@@ -1,0 +1,289 @@
+// Device code shared by the sweep and the adjoint: storage forms, per-launch
+// coefficients, the pull gather, the TRT collision, the sweep kernel and the
+// fixed-order reductions.  Included by sweep.cu and adjoint.cu; everything
+// here has internal linkage.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+namespace {
+
+template <int PREC>
+struct Form;
+template <>
+struct Form<LBM_F64> {
+  using S = double;
+  using C = double;
+  static constexpr bool kShifted = false;
+};
+template <>
+struct Form<LBM_F32> {
+  using S = float;
+  using C = float;
+  static constexpr bool kShifted = false;
+};
+template <>
+struct Form<LBM_F32S> {
+  using S = float;
+  using C = float;
+  static constexpr bool kShifted = true;
+};
+template <>
+struct Form<LBM_F16S> {
+  using S = __half;
+  using C = float;
+  static constexpr bool kShifted = true;
+};
+template <>
+struct Form<LBM_BF16S> {
+  using S = __nv_bfloat16;
+  using C = float;
+  static constexpr bool kShifted = true;
+};
+
+// Per-launch coefficients in the arithmetic precision C.
+template <class C>
+struct Coef {
+  C hp, hm;        // (1 - w+)/2, (1 - w-)/2
+  C one_m_wp;      // 1 - w+
+  C w0p, w1p;      // w+ / 3, w+ / 18
+  C k1, k2;        // 4.5 w+ / 18, 4.5 w+ / 36
+  C a1, b1;        // 3 w- / 18, 3 (1 - w-/2) / 18
+  C F[3], hF[3];   // F, F / 2
+  C bF1[3];        // b1 F (used without damping)
+  C scale, inv_scale;
+};
+
+template <class C>
+Coef<C> make_coef(double wp, double wm, const double F[3], int scale_exp) {
+  Coef<C> k;
+  k.hp = (C)(0.5 * (1.0 - wp));
+  k.hm = (C)(0.5 * (1.0 - wm));
+  k.one_m_wp = (C)(1.0 - wp);
+  k.w0p = (C)(wp / 3.0);
+  k.w1p = (C)(wp / 18.0);
+  k.k1 = (C)(4.5 * wp / 18.0);
+  k.k2 = (C)(4.5 * wp / 36.0);
+  k.a1 = (C)(3.0 * wm / 18.0);
+  const double b1 = 3.0 * (1.0 - 0.5 * wm) / 18.0;
+  k.b1 = (C)b1;
+  for (int d = 0; d < 3; ++d) {
+    k.F[d] = (C)F[d];
+    k.hF[d] = (C)(0.5 * F[d]);
+    k.bF1[d] = (C)(b1 * F[d]);
+  }
+  k.scale = (C)std::ldexp(1.0, scale_exp);
+  k.inv_scale = (C)std::ldexp(1.0, -scale_exp);
+  return k;
+}
+
+// ---- storage conversion -------------------------------------------------
+template <int PREC>
+__device__ __forceinline__ typename Form<PREC>::C decode(typename Form<PREC>::S v,
+                                                         typename Form<PREC>::C inv_scale) {
+  if constexpr (PREC == LBM_F16S) return __half2float(v) * inv_scale;
+  else if constexpr (PREC == LBM_BF16S) return __bfloat162float(v) * inv_scale;
+  else return v;
+}
+
+template <int PREC>
+__device__ __forceinline__ typename Form<PREC>::S encode(typename Form<PREC>::C v,
+                                                         typename Form<PREC>::C scale) {
+  if constexpr (PREC == LBM_F16S) return __float2half_rn(v * scale);
+  else if constexpr (PREC == LBM_BF16S) return __float2bfloat16_rn(v * scale);
+  else return v;
+}
+
+template <int PREC>
+__device__ __forceinline__ typename Form<PREC>::S load_ro(const typename Form<PREC>::S* p) {
+  if constexpr (PREC == LBM_F16S) {
+    return __ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p)));
+  } else if constexpr (PREC == LBM_BF16S) {
+    return __ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p)));
+  } else {
+    return __ldg(p);
+  }
+}
+
+template <int PREC>
+__device__ __forceinline__ void store_stream(typename Form<PREC>::S* p, typename Form<PREC>::S v) {
+  if constexpr (PREC == LBM_F16S) {
+    __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(v));
+  } else if constexpr (PREC == LBM_BF16S) {
+    __stcs(reinterpret_cast<unsigned short*>(p), __bfloat16_as_ushort(v));
+  } else {
+    __stcs(p, v);
+  }
+}
+
+// ---- the collision ----------------------------------------------------------
+// g[19] in: pulled PDFs (or deviations); out: post-collision values.
+template <class C, bool DAMPED>
+__device__ __forceinline__ void collide(C g[19], const Coef<C>& k, C alpha, C& rho_out,
+                                        C u_out[3]) {
+  C s[9], d[9];
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    s[p] = g[2 * p + 1] + g[2 * p + 2];
+    d[p] = g[2 * p + 1] - g[2 * p + 2];
+  }
+  // pairs: 0:(1,2)=+x 1:(3,4)=+y 2:(5,6)=+z 3:(7,8)=(1,1,0) 4:(9,10)=(1,-1,0)
+  // 5:(11,12)=(1,0,1) 6:(13,14)=(1,0,-1) 7:(15,16)=(0,1,1) 8:(17,18)=(0,1,-1)
+  const C rho = g[0] + (((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])) + s[8]);
+  const C jx = ((d[0] + d[3]) + (d[4] + d[5])) + d[6];
+  const C jy = ((d[1] + d[3]) - (d[4] - d[7])) + d[8];
+  const C jz = ((d[2] + d[5]) - (d[6] - d[7])) - d[8];
+  C ux, uy, uz, Vx, Vy, Vz;
+  if constexpr (DAMPED) {
+    const C ia = C(1) / (C(1) + C(0.5) * alpha);
+    ux = (jx + k.hF[0]) * ia;
+    uy = (jy + k.hF[1]) * ia;
+    uz = (jz + k.hF[2]) * ia;
+    Vx = k.a1 * ux + k.b1 * (k.F[0] - alpha * ux);
+    Vy = k.a1 * uy + k.b1 * (k.F[1] - alpha * uy);
+    Vz = k.a1 * uz + k.b1 * (k.F[2] - alpha * uz);
+  } else {
+    ux = jx + k.hF[0];
+    uy = jy + k.hF[1];
+    uz = jz + k.hF[2];
+    Vx = k.a1 * ux + k.bF1[0];
+    Vy = k.a1 * uy + k.bF1[1];
+    Vz = k.a1 * uz + k.bF1[2];
+  }
+  const C usq = ux * ux + uy * uy + uz * uz;
+  const C rp = rho - C(1.5) * usq;
+  const C R1 = k.w1p * rp, R2 = C(0.5) * R1;
+  g[0] = k.one_m_wp * g[0] + k.w0p * rp;
+#define LBM_PAIR(P, CU, CV, R, K, HALF)                    \
+  {                                                        \
+    const C cu_ = (CU);                                    \
+    const C cv_ = HALF ? C(0.5) * (CV) : (CV);             \
+    const C P_ = k.hp * s[P] + (K * (cu_ * cu_) + R);      \
+    const C Q_ = k.hm * d[P] + cv_;                        \
+    g[2 * P + 1] = P_ + Q_;                                \
+    g[2 * P + 2] = P_ - Q_;                                \
+  }
+  LBM_PAIR(0, ux, Vx, R1, k.k1, false)
+  LBM_PAIR(1, uy, Vy, R1, k.k1, false)
+  LBM_PAIR(2, uz, Vz, R1, k.k1, false)
+  LBM_PAIR(3, ux + uy, Vx + Vy, R2, k.k2, true)
+  LBM_PAIR(4, ux - uy, Vx - Vy, R2, k.k2, true)
+  LBM_PAIR(5, ux + uz, Vx + Vz, R2, k.k2, true)
+  LBM_PAIR(6, ux - uz, Vx - Vz, R2, k.k2, true)
+  LBM_PAIR(7, uy + uz, Vy + Vz, R2, k.k2, true)
+  LBM_PAIR(8, uy - uz, Vy - Vz, R2, k.k2, true)
+#undef LBM_PAIR
+  rho_out = rho;
+  u_out[0] = ux;
+  u_out[1] = uy;
+  u_out[2] = uz;
+}
+
+// Fixed-order block reduction of 4 doubles; thread 0 writes out[0..3].
+__device__ __forceinline__ void block_sum4(double v[4], double* out) {
+  __shared__ double sm[kSweepThreads / 32][4];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sm[warp][j] = v[j];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double acc = 0.0;
+#pragma unroll
+    for (int w = 0; w < kSweepThreads / 32; ++w) acc += sm[w][threadIdx.x];
+    out[threadIdx.x] = acc;
+  }
+}
+
+// Gathers the 19 pulled values of cell i.
+template <int PREC>
+__device__ __forceinline__ void gather(const typename Form<PREC>::S* __restrict__ src,
+                                       const int32_t* __restrict__ adj, int32_t n, int32_t i,
+                                       typename Form<PREC>::C inv_scale,
+                                       typename Form<PREC>::C g[19]) {
+  int32_t idx[18];
+#pragma unroll
+  for (int q = 0; q < 18; ++q) idx[q] = __ldcs(adj + q * n + i);
+  g[0] = decode<PREC>(load_ro<PREC>(src + i), inv_scale);
+#pragma unroll
+  for (int q = 1; q < 19; ++q) g[q] = decode<PREC>(load_ro<PREC>(src + idx[q - 1]), inv_scale);
+}
+
+template <int PREC, bool DAMPED, bool REDUCE>
+__global__ void __launch_bounds__(kSweepThreads)
+    sweep_kernel(const typename Form<PREC>::S* __restrict__ src,
+                 typename Form<PREC>::S* __restrict__ dst, const int32_t* __restrict__ adj,
+                 int32_t n, Coef<typename Form<PREC>::C> k,
+                 const typename Form<PREC>::C* __restrict__ alpha, double* __restrict__ partials) {
+  using C = typename Form<PREC>::C;
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < n) {
+    C g[19];
+    gather<PREC>(src, adj, n, i, k.inv_scale, g);
+    C rho, u[3];
+    collide<C, DAMPED>(g, k, DAMPED ? alpha[i] : C(0), rho, u);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) store_stream<PREC>(dst + q * n + i, encode<PREC>(g[q], k.scale));
+    if (REDUCE) {
+      red[0] = (double)rho;
+      red[1] = (double)u[0];
+      red[2] = (double)u[1];
+      red[3] = (double)u[2];
+    }
+  }
+  if (REDUCE) block_sum4(red, partials + 4 * (int64_t)blockIdx.x);
+}
+
+// Per-cell moments of the collision that a step from `src` performs.
+template <int PREC, bool DAMPED>
+__global__ void __launch_bounds__(kSweepThreads)
+    moments_kernel(const typename Form<PREC>::S* __restrict__ src, const int32_t* __restrict__ adj,
+                   int32_t n, Coef<typename Form<PREC>::C> k,
+                   const typename Form<PREC>::C* __restrict__ alpha, double* __restrict__ rho_out,
+                   double* __restrict__ u_out) {
+  using C = typename Form<PREC>::C;
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  if (i >= n) return;
+  C g[19];
+  gather<PREC>(src, adj, n, i, k.inv_scale, g);
+  C rho, u[3];
+  collide<C, DAMPED>(g, k, DAMPED ? alpha[i] : C(0), rho, u);
+  rho_out[i] = Form<PREC>::kShifted ? 1.0 + (double)rho : (double)rho;
+  u_out[i] = (double)u[0];
+  u_out[n + i] = (double)u[1];
+  u_out[2 * (int64_t)n + i] = (double)u[2];
+}
+
+// Final fixed-order sum of the block partials: out[j] = sum_b part[4 b + j].
+__global__ void __launch_bounds__(1024)
+    final_sum_kernel(const double* __restrict__ part, int64_t nblocks, double* out) {
+  __shared__ double sm[1024][4];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t b = threadIdx.x; b < nblocks; b += 1024)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] += part[4 * b + j];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sm[threadIdx.x][j] = acc[j];
+  __syncthreads();
+  for (int s = 512; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sm[threadIdx.x][j] += sm[threadIdx.x + s][j];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) out[threadIdx.x] = sm[0][threadIdx.x];
+}
+
+}  // namespace
+}  // namespace lbm

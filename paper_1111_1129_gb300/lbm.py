@@ -211,3 +211,69 @@ class LBMState:
             self.close()
         except Exception:
             pass
+
+
+class Adjoint:
+    """Checkpointed reverse pass for K steps of a state (``lbm_adjoint_*``)."""
+
+    def __init__(self, state: LBMState, n_steps: int, stride: int = 0):
+        self.state = state
+        self.n_steps = int(n_steps)
+        self._handle = None
+        self._handle = capi.lbm_adjoint_create(state.handle, self.n_steps, int(stride))
+
+    @property
+    def handle(self) -> int:
+        return self._handle
+
+    def forward(self, omega_plus: float, omega_minus: float, force, axis: int) -> float:
+        """J = mean u_axis of the collision of step K, from the state's
+        current PDFs (the state is not advanced)."""
+        return capi.lbm_adjoint_forward(self._handle, omega_plus, omega_minus, force, axis)
+
+    def backward(self, want_alpha: bool = True, want_f0: bool = False):
+        """(dJ/dF [3] tuple, dJ/dalpha [N] or None, dJ/df0 [19, N] or None)."""
+        n = self.state.n
+        da = torch.empty(n, dtype=torch.float64, device="cuda") if want_alpha else None
+        df0 = torch.empty((19, n), dtype=torch.float64, device="cuda") if want_f0 else None
+        dF = capi.lbm_adjoint_backward(self._handle, None if da is None else da.data_ptr(),
+                                       None if df0 is None else df0.data_ptr())
+        return dF, da, df0
+
+    def close(self):
+        if self._handle:
+            capi.lbm_free(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LBMFlux(torch.autograd.Function):
+    """Differentiable mean axial velocity after K steps.
+
+    ``LBMFlux.apply(force, alpha, adjoint, omega_plus, omega_minus, axis)``
+    with force a float64 tensor [3] and alpha a float64 tensor [N] (fluid
+    order) or None returns J as a 0-d float64 tensor; backward runs the
+    checkpointed adjoint and returns dJ/dF and dJ/dalpha."""
+
+    @staticmethod
+    def forward(ctx, force, alpha, adjoint: Adjoint, omega_plus, omega_minus, axis):
+        st = adjoint.state
+        if alpha is not None:
+            st.set_damping(alpha.detach())
+        J = adjoint.forward(omega_plus, omega_minus, force.detach().cpu().tolist(), axis)
+        ctx.adjoint = adjoint
+        ctx.has_alpha = alpha is not None
+        ctx.force_device = force.device
+        return torch.tensor(J, dtype=torch.float64, device=force.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        dF, da, _ = ctx.adjoint.backward(want_alpha=ctx.has_alpha)
+        grad_force = gJ * torch.tensor(dF, dtype=torch.float64, device=ctx.force_device)
+        grad_alpha = gJ.to(da.device) * da if ctx.has_alpha else None
+        return grad_force, grad_alpha, None, None, None, None
