@@ -384,6 +384,72 @@ def run_precision_study(args):
     return 0
 
 
+def run_batch_study(args):
+    """256 packed beds (cube sides uniform in {24..96}, sphere radii in
+    [3, 8], forces in [1e-7, 1e-5] along z), FP32 shifted storage: the
+    autotuned batched launch under a CUDA graph against the same beds
+    stepped one by one; per-bed fluxes are compared bit for bit."""
+    import torch
+
+    from paper_1111_1129_gb300 import (BatchedState, LBMState, SparseLattice, capi, inputs,
+                                       omega_minus)
+
+    capi.load()
+    wm = omega_minus(WP)
+    beds, fz = inputs.batch_beds(256, 0)
+    forces = [(0.0, 0.0, float(f)) for f in fz]
+    lats = [SparseLattice(torch.from_numpy(b.flags).cuda(), "blocked", (8, 8, 8), b.periodic)
+            for b in beds]
+    n_fluid = sum(l.n for l in lats)
+    K = args.batch_steps
+    tuner = BatchedState(lats, "f32s")
+    block, cpt, cand = tuner.tune(20, WP, wm, forces)
+    tuner.close()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    out = {}
+    for label, graph in (("batched_graph", True), ("batched_no_graph", False)):
+        bs = BatchedState(lats, "f32s")
+        bs.configure(block, cpt, graph)
+        bs.step(K, WP, wm, forces)          # warm-up; captures the graph
+        bs.reset()                          # back to rest, same grid parity
+        ms = timed(lambda: bs.step(K, WP, wm, forces))
+        mass, flux = bs.reduce_flux(2)
+        out[label] = {"mflups": n_fluid * K / (ms * 1e-3) / 1e6, "ms": ms}
+        if graph:
+            batched_flux = flux
+        bs.close()
+    states = [LBMState(l, "f32s") for l in lats]
+
+    def separate():
+        for st, F in zip(states, forces):
+            st.step(K, WP, wm, F)
+
+    ms = timed(separate)
+    same = sum(1 for st, q in zip(states, batched_flux) if st.reduce_flux(2)[1] == q)
+    out["separate_loops"] = {"mflups": n_fluid * K / (ms * 1e-3) / 1e6, "ms": ms}
+    for st in states:
+        st.close()
+    for l in lats:
+        l.close()
+    line = {"study": "batched beds", "n_beds": 256, "fluid_cells": n_fluid, "steps": K,
+            "precision": "f32s", "tuned": {"block": block, "cells_per_thread": cpt,
+                                           "candidate_ms_block_major": cand},
+            **out, "speedup_vs_separate": out["batched_graph"]["mflups"] /
+            out["separate_loops"]["mflups"],
+            "per_bed_flux_bit_identical": f"{same}/256"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -401,11 +467,16 @@ def main():
     ap.add_argument("--precision-study", action="store_true",
                     help="run the storage-precision study instead of the benchmark")
     ap.add_argument("--study-steps", type=int, default=20000)
+    ap.add_argument("--batch-study", action="store_true",
+                    help="run the 256-bed batching study instead of the benchmark")
+    ap.add_argument("--batch-steps", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.precision_study:
         return run_precision_study(args)
+    if args.batch_study:
+        return run_batch_study(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -150,6 +150,10 @@ int lbm_state_create(const lbm_sparse* sp, int32_t precision, int32_t scale_exp,
 int lbm_state_set_pdfs(lbm_state* st, const double* f_dev);
 int lbm_state_get_pdfs(const lbm_state* st, double* f_dev);
 
+/* Put the current PDFs back to rest (f_q = w_q) and clear the step count;
+ * which of the two grids is current does not change. */
+int lbm_state_reset(lbm_state* st);
+
 /*
  * Per-cell Brinkman damping alpha_n >= 0 in fluid order (device FP64[N]),
  * copied into the state in its arithmetic precision; NULL removes damping.
@@ -229,6 +233,43 @@ int lbm_step_f64_noalloc(const double* f_src_dev, double* f_dst_dev, const int32
                          int64_t n_fluid, double omega_plus, double omega_minus,
                          const double force[3], const double* alpha_dev, double* sums_dev,
                          void* stream);
+
+/* ---- batches of independent beds ----------------------------------------
+ * Many packed beds of uneven size stepped by one launch per time step:
+ * their cell lists are concatenated (each bed padded to a multiple of 2048
+ * cells), each bed has its own body force, and each bed's flux is reduced
+ * separately.  A bed's PDFs and flux are bit-identical to stepping it alone.
+ *
+ * lbm_state_create_batched: beds[n_beds] built on the same stream (they
+ *   may be released afterwards; the state keeps a remapped copy of their
+ *   adjacency).  PDF arrays of the state (lbm_state_get/set_pdfs) have the
+ *   padded length N_pad; see lbm_batch_layout.  Damping, moments and the
+ *   adjoint are not available on a batched state.
+ * lbm_step on a batched state takes force = host double[n_beds][3];
+ *   lbm_reduce_flux writes mass_out[n_beds] and flux_out[n_beds].  The K
+ *   launches of one lbm_step call are captured once into a CUDA graph and
+ *   replayed while K, the relaxation rates and the launch shape stay the
+ *   same (forces may change between calls).
+ */
+int lbm_state_create_batched(const lbm_sparse* const* beds, int32_t n_beds, int32_t precision,
+                             int32_t scale_exp, lbm_state** out);
+
+/* begin_out[n_beds]: first padded index of each bed; count_out[n_beds]:
+ * its fluid cells; *n_padded: N_pad.  Any out pointer may be NULL. */
+int lbm_batch_layout(const lbm_state* st, int32_t* n_beds, int64_t* begin_out,
+                     int64_t* count_out, int64_t* n_padded);
+
+/* Launch shape of the non-reducing steps: block in {128, 256, 512}, cells
+ * per thread in {1, 2, 4}; use_graph 0/1.  Results do not depend on it. */
+int lbm_batch_config(lbm_state* st, int32_t block, int32_t cells_per_thread, int32_t use_graph);
+
+/* Autotuner: times steps_per_candidate steps under each of the nine launch
+ * shapes (advancing the state by 9 * (steps_per_candidate + 1) steps, whose
+ * result does not depend on the shapes), keeps the fastest, and returns it
+ * (ms_out[9], if given, receives each candidate's time in ms, block-major). */
+int lbm_batch_tune(lbm_state* st, int32_t steps_per_candidate, double omega_plus,
+                   double omega_minus, const double* forces, int32_t* block_out,
+                   int32_t* cpt_out, float* ms_out);
 
 /* ---- adjoint (reverse mode) ---------------------------------------------
  * Gradients of J = (1/N) sum_n u_axis,n, the mean axial velocity of the

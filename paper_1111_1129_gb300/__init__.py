@@ -9,7 +9,7 @@ loads nothing; the library is loaded on first use and its absence is an
 error, never a fallback.
 """
 
-__all__ = ["SparseLattice", "LBMState", "Adjoint", "LBMFlux", "omega_minus", "ordering_keys",
+__all__ = ["SparseLattice", "LBMState", "Adjoint", "LBMFlux", "BatchedState", "omega_minus", "ordering_keys",
            "deviation_bound", "shifted_scale_exp"]
 
 

@@ -36,6 +36,7 @@ SIGNATURES = {
     "lbm_state_create": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
     "lbm_state_set_pdfs": (ctypes.c_int, [_vp, _vp]),
     "lbm_state_get_pdfs": (ctypes.c_int, [_vp, _vp]),
+    "lbm_state_reset": (ctypes.c_int, [_vp]),
     "lbm_set_damping": (ctypes.c_int, [_vp, _vp]),
     "lbm_step": (ctypes.c_int, [_vp, _i32, _d, _d, _vp]),
     "lbm_reduce_flux": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
@@ -44,6 +45,10 @@ SIGNATURES = {
     "lbm_synchronize": (ctypes.c_int, [_vp, _d]),
     "lbm_set_timeout": (None, [_d]),
     "lbm_step_f64_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i64, _d, _d, _vp, _vp, _vp, _vp]),
+    "lbm_state_create_batched": (ctypes.c_int, [_vp, _i32, _i32, _i32, _vp]),
+    "lbm_batch_layout": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "lbm_batch_config": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
+    "lbm_batch_tune": (ctypes.c_int, [_vp, _i32, _d, _d, _vp, _vp, _vp, _vp]),
     "lbm_adjoint_create": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
     "lbm_adjoint_forward": (ctypes.c_int, [_vp, _d, _d, _vp, _i32, _vp]),
     "lbm_adjoint_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -132,6 +137,10 @@ def lbm_state_get_pdfs(state: int, f_dev: int) -> None:
     _check(load().lbm_state_get_pdfs(state, f_dev))
 
 
+def lbm_state_reset(state: int) -> None:
+    _check(load().lbm_state_reset(state))
+
+
 def lbm_set_damping(state: int, alpha_dev) -> None:
     _check(load().lbm_set_damping(state, alpha_dev))
 
@@ -164,6 +173,59 @@ def lbm_synchronize(state: int, timeout_s: float = 0.0) -> None:
 
 def lbm_set_timeout(timeout_s: float) -> None:
     load().lbm_set_timeout(float(timeout_s))
+
+
+def lbm_state_create_batched(sparses, precision: int, scale_exp: int = 0) -> int:
+    arr = (ctypes.c_void_p * len(sparses))(*sparses)
+    out = ctypes.c_void_p()
+    _check(load().lbm_state_create_batched(arr, len(sparses), int(precision), int(scale_exp),
+                                           ctypes.byref(out)))
+    return out.value
+
+
+def lbm_batch_layout(state: int):
+    """(begin [n_beds], count [n_beds], n_padded) as Python lists/int."""
+    nb = ctypes.c_int32()
+    _check(load().lbm_batch_layout(state, ctypes.byref(nb), None, None, None))
+    begin = (ctypes.c_int64 * nb.value)()
+    count = (ctypes.c_int64 * nb.value)()
+    npad = ctypes.c_int64()
+    _check(load().lbm_batch_layout(state, None, begin, count, ctypes.byref(npad)))
+    return list(begin), list(count), npad.value
+
+
+def lbm_batch_config(state: int, block: int, cells_per_thread: int, use_graph: bool) -> None:
+    _check(load().lbm_batch_config(state, int(block), int(cells_per_thread), int(bool(use_graph))))
+
+
+def _forces(forces):
+    flat = [float(v) for row in forces for v in row]
+    return (ctypes.c_double * len(flat))(*flat)
+
+
+def lbm_step_batched(state: int, n_steps: int, omega_plus: float, omega_minus: float,
+                     forces) -> None:
+    """lbm_step on a batched state; forces is a sequence of (Fx, Fy, Fz)."""
+    _check(load().lbm_step(state, int(n_steps), float(omega_plus), float(omega_minus),
+                           _forces(forces)))
+
+
+def lbm_reduce_flux_batched(state: int, axis: int, n_beds: int):
+    m = (ctypes.c_double * n_beds)()
+    q = (ctypes.c_double * n_beds)()
+    _check(load().lbm_reduce_flux(state, int(axis), m, q))
+    return list(m), list(q)
+
+
+def lbm_batch_tune(state: int, steps_per_candidate: int, omega_plus: float, omega_minus: float,
+                   forces):
+    """(block, cells_per_thread, [9 candidate times in ms])."""
+    b, c = ctypes.c_int32(), ctypes.c_int32()
+    ms = (ctypes.c_float * 9)()
+    _check(load().lbm_batch_tune(state, int(steps_per_candidate), float(omega_plus),
+                                 float(omega_minus), _forces(forces), ctypes.byref(b),
+                                 ctypes.byref(c), ms))
+    return b.value, c.value, list(ms)
 
 
 def lbm_adjoint_create(state: int, n_steps: int, stride: int = 0) -> int:

@@ -416,6 +416,7 @@ extern "C" int lbm_adjoint_create(const lbm_state* st, int32_t n_steps, int32_t 
   if (!out) return fail(LBM_EINVAL, "out is NULL");
   *out = nullptr;
   if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  if (st->batch) return fail(LBM_EINVAL, "the adjoint is not available on a batched state");
   if (n_steps < 1) return fail(LBM_EINVAL, "n_steps = %d must be >= 1", n_steps);
   if (stride < 0) return fail(LBM_EINVAL, "checkpoint stride %d < 0", stride);
   if (stride == 0) stride = (int32_t)std::ceil(std::sqrt((double)n_steps));

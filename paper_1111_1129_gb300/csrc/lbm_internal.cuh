@@ -157,6 +157,30 @@ struct lbm_sparse {
   cudaStream_t stream;
 };
 
+namespace lbm {
+// Batched state: beds concatenated, each padded to kBatchChunk cells so that
+// every tile of every launch configuration lies inside one bed.
+constexpr int64_t kBatchChunk = 2048;
+struct Batch {
+  int32_t n_beds;
+  int64_t* h_begin;      // [n_beds] first padded-list index of each bed (host)
+  int64_t* h_count;      // [n_beds] fluid cells of each bed (host)
+  int64_t* d_begin;      // device copies
+  int32_t* d_count;
+  int32_t* d_chunk_bed;  // [n_pad / kBatchChunk] bed of each chunk
+  void* d_force;         // [n_beds] per-bed force constants (arithmetic type)
+  void* h_force;         // pinned staging for d_force
+  double* d_red;         // [n_beds][4] per-bed final sums
+  double* h_red;         // pinned
+  int block, cpt;        // launch configuration of the non-reducing steps
+  cudaStream_t capture;  // private stream used to capture graphs
+  cudaGraphExec_t graph; // cached K-step graph (or null)
+  int32_t g_steps, g_parity, g_block, g_cpt;
+  double g_wp, g_wm;
+  int use_graph;
+};
+}  // namespace lbm
+
 struct lbm_state {
   uint32_t magic;
   const lbm_sparse* sp;
@@ -173,6 +197,7 @@ struct lbm_state {
   double last_force[3];
   double last_wp, last_wm;
   cudaEvent_t done;    // recorded to wait for the stream with a time limit
+  lbm::Batch* batch;   // non-null for a batched state (sp is then owned)
 };
 
 namespace lbm {
@@ -185,4 +210,8 @@ bool valid_state(const lbm_state* st);
 // Records `ev` on `stream` and polls it with a wall-clock limit (<= 0: the
 // library default); LBM_ETIMEOUT if the work is still running then.
 int wait_event(cudaEvent_t ev, cudaStream_t stream, double timeout_s);
+// Batched-state hooks (batch.cu).
+int batch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const double* forces);
+int batch_reduce(lbm_state* st, int32_t axis, double* mass_out, double* flux_out);
+void free_batch(lbm_state* st);
 }  // namespace lbm

@@ -197,6 +197,7 @@ void free_state(lbm_state* st) {
     if (p) cudaFree(p);
   if (st->red_host) cudaFreeHost(st->red_host);
   if (st->done) cudaEventDestroy(st->done);
+  if (st->batch) free_batch(st);
   st->magic = 0;
   delete st;
 }
@@ -251,21 +252,29 @@ extern "C" int lbm_state_create(const lbm_sparse* sp, int32_t precision, int32_t
 extern "C" int lbm_state_set_pdfs(lbm_state* st, const double* f_dev) {
   clear_error();
   if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
-  if (!f_dev) return fail(LBM_EINVAL, "f_dev is NULL");
+  if (!f_dev && st->sp->n > 0) return fail(LBM_EINVAL, "f_dev is NULL");
   st->steps = 0;
   return dispatch_set(st, f_dev, 0);
+}
+
+extern "C" int lbm_state_reset(lbm_state* st) {
+  clear_error();
+  if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  st->steps = 0;
+  return dispatch_set(st, nullptr, 1);
 }
 
 extern "C" int lbm_state_get_pdfs(const lbm_state* st, double* f_dev) {
   clear_error();
   if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
-  if (!f_dev) return fail(LBM_EINVAL, "f_dev is NULL");
+  if (!f_dev && st->sp->n > 0) return fail(LBM_EINVAL, "f_dev is NULL");
   return dispatch_get(st, f_dev);
 }
 
 extern "C" int lbm_set_damping(lbm_state* st, const double* alpha_dev) {
   clear_error();
   if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  if (st->batch) return fail(LBM_EINVAL, "damping is not supported on a batched state");
   if (!alpha_dev) {
     if (st->alpha) {
       cudaStreamSynchronize(st->sp->stream);
@@ -302,10 +311,12 @@ extern "C" int lbm_step(lbm_state* st, int32_t n_steps, double omega_plus, doubl
   if (!(omega_plus > 0.0 && omega_plus < 2.0) || !(omega_minus > 0.0 && omega_minus < 2.0))
     return fail(LBM_EINVAL, "relaxation rates must lie in (0, 2): %g, %g", omega_plus, omega_minus);
   if (!force) return fail(LBM_EINVAL, "force is NULL");
-  for (int d = 0; d < 3; ++d)
+  const int n_force = st->batch ? 3 * st->batch->n_beds : 3;
+  for (int d = 0; d < n_force; ++d)
     if (!std::isfinite(force[d])) return fail(LBM_EINVAL, "force[%d] is not finite", d);
   if (n_steps == 0) return LBM_OK;
-  const int rc = dispatch_steps(st, n_steps, omega_plus, omega_minus, force);
+  const int rc = st->batch ? batch_steps(st, n_steps, omega_plus, omega_minus, force)
+                           : dispatch_steps(st, n_steps, omega_plus, omega_minus, force);
   if (rc != LBM_OK) return rc;
   st->steps += n_steps;
   st->last_wp = omega_plus;
@@ -319,6 +330,7 @@ extern "C" int lbm_reduce_flux(lbm_state* st, int32_t axis, double* mass_out, do
   if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
   if (axis < 0 || axis > 2) return fail(LBM_EINVAL, "axis %d outside {0,1,2}", axis);
   if (st->steps < 1) return fail(LBM_EINVAL, "no step taken yet");
+  if (st->batch) return batch_reduce(st, axis, mass_out, flux_out);
   const cudaStream_t stream = st->sp->stream;
   const int64_t n = st->sp->n;
   if (n > 0) {
@@ -344,8 +356,9 @@ extern "C" int lbm_reduce_flux(lbm_state* st, int32_t axis, double* mass_out, do
 extern "C" int lbm_moments(const lbm_state* st, double* rho_dev, double* u_dev) {
   clear_error();
   if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
-  if (!rho_dev || !u_dev) return fail(LBM_EINVAL, "rho_dev / u_dev is NULL");
+  if ((!rho_dev || !u_dev) && st->sp->n > 0) return fail(LBM_EINVAL, "rho_dev / u_dev is NULL");
   if (st->steps < 1) return fail(LBM_EINVAL, "no step taken yet");
+  if (st->batch) return fail(LBM_EINVAL, "lbm_moments is not available on a batched state");
   return dispatch_moments(st, rho_dev, u_dev);
 }
 

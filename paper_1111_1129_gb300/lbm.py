@@ -277,3 +277,68 @@ class LBMFlux(torch.autograd.Function):
         grad_force = gJ * torch.tensor(dF, dtype=torch.float64, device=ctx.force_device)
         grad_alpha = gJ.to(da.device) * da if ctx.has_alpha else None
         return grad_force, grad_alpha, None, None, None, None
+
+
+class BatchedState:
+    """Many independent beds stepped together (``lbm_state_create_batched``).
+
+    Each bed keeps its own force; per-bed results are bit-identical to
+    stepping the bed alone."""
+
+    def __init__(self, lattices, precision: str = "f32s", scale_exp: int = 0):
+        self.lattices = list(lattices)
+        self.precision = precision
+        self._handle = None
+        self._handle = capi.lbm_state_create_batched([l.handle for l in self.lattices],
+                                                     PRECISIONS[precision], scale_exp)
+        self.begin, self.count, self.n_padded = capi.lbm_batch_layout(self._handle)
+
+    @property
+    def handle(self) -> int:
+        return self._handle
+
+    @property
+    def n_beds(self) -> int:
+        return len(self.lattices)
+
+    @property
+    def n_fluid(self) -> int:
+        return int(sum(self.count))
+
+    def configure(self, block: int = 256, cells_per_thread: int = 1, use_graph: bool = True):
+        capi.lbm_batch_config(self._handle, block, cells_per_thread, use_graph)
+
+    def tune(self, steps_per_candidate: int, omega_plus: float, omega_minus: float, forces):
+        """Pick the fastest launch shape (advances the state)."""
+        return capi.lbm_batch_tune(self._handle, steps_per_candidate, omega_plus, omega_minus,
+                                   forces)
+
+    def step(self, n_steps: int, omega_plus: float, omega_minus: float, forces) -> None:
+        capi.lbm_step_batched(self._handle, n_steps, omega_plus, omega_minus, forces)
+
+    def reduce_flux(self, axis: int):
+        """(mass [n_beds], flux [n_beds]) of the most recent step."""
+        return capi.lbm_reduce_flux_batched(self._handle, axis, self.n_beds)
+
+    def reset(self) -> None:
+        """Back to rest, keeping the captured graph valid."""
+        capi.lbm_state_reset(self._handle)
+
+    def get_pdfs(self, bed: int = None) -> torch.Tensor:
+        f = torch.empty((19, self.n_padded), dtype=torch.float64, device="cuda")
+        capi.lbm_state_get_pdfs(self._handle, f.data_ptr())
+        if bed is None:
+            return f
+        b, c = self.begin[bed], self.count[bed]
+        return f[:, b:b + c]
+
+    def close(self):
+        if self._handle:
+            capi.lbm_free(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

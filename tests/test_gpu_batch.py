@@ -1,0 +1,130 @@
+"""Batched beds (one launch per step over concatenated cell lists, per-bed
+forces, CUDA graph, tuned launch shape): every bed's PDFs and flux must be
+bit-identical to stepping that bed alone, whatever the launch shape."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1111_1129_gb300 import (BatchedState, LBMState, SparseLattice, build, capi, inputs,
+                                   omega_minus)
+
+pytestmark = pytest.mark.gpu
+
+WP = 1.0 / 0.8
+WM = omega_minus(WP)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    capi.load()
+
+
+def _beds(n=7, seed=2):
+    rng = np.random.default_rng(seed)
+    beds = []
+    for b in range(n):
+        s = int(rng.integers(12, 34))
+        beds.append(inputs.packed_bed((s, s, s), 2, s - 2.0, float(rng.uniform(2.5, 5)), 0.0,
+                                      100 + b))
+    # one bed with no fluid at all
+    beds.append(inputs.packed_bed((8, 8, 8), 2, 0.5, 0.0, 0.0, 0))
+    forces = [(1e-6 * (b + 1), -2e-7 * b, 1e-5 / (b + 1)) for b in range(len(beds))]
+    return beds, forces
+
+
+def _lattices(beds):
+    return [SparseLattice(torch.from_numpy(b.flags).cuda(), "blocked", (8, 8, 8), b.periodic)
+            for b in beds]
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32s", "f16s"])
+def test_batched_beds_bit_identical_to_separate_runs(precision):
+    beds, forces = _beds()
+    lats = _lattices(beds)
+    assert lats[-1].n == 0
+    steps = 37
+    ref_f, ref_flux = [], []
+    for lat, F in zip(lats, forces):
+        st = LBMState(lat, precision, 20)
+        st.step(steps, WP, WM, F)
+        ref_f.append(st.get_pdfs().cpu().numpy())
+        ref_flux.append(st.reduce_flux(2) if lat.n > 0 else None)
+        st.close()
+    for block, cpt, graph in [(256, 1, True), (128, 4, True), (512, 2, False), (512, 4, True)]:
+        bs = BatchedState(lats, precision, 20)
+        bs.configure(block, cpt, graph)
+        bs.step(steps, WP, WM, forces)
+        mass, flux = bs.reduce_flux(2)
+        f_all = bs.get_pdfs().cpu().numpy()
+        for i in range(len(lats)):
+            b, c = bs.begin[i], bs.count[i]
+            assert b % 2048 == 0
+            np.testing.assert_array_equal(f_all[:, b:b + c], ref_f[i])
+            if ref_flux[i] is not None:
+                assert (mass[i], flux[i]) == ref_flux[i]
+            else:
+                assert (mass[i], flux[i]) == (0.0, 0.0)
+        bs.close()
+    for lat in lats:
+        lat.close()
+
+
+def test_graph_replay_follows_new_forces():
+    beds, forces = _beds(4, seed=3)
+    lats = _lattices(beds)
+    bs = BatchedState(lats, "f32s")
+    bs.step(10, WP, WM, forces)
+    forces2 = [(f[0] * 3, f[1], -f[2]) for f in forces]
+    bs.step(10, WP, WM, forces2)          # same K: the cached graph is replayed
+    _, flux = bs.reduce_flux(2)
+    for i, lat in enumerate(lats[:-1]):
+        st = LBMState(lat, "f32s")
+        st.step(10, WP, WM, forces[i])
+        st.step(10, WP, WM, forces2[i])
+        assert st.reduce_flux(2)[1] == flux[i]
+        st.close()
+    bs.close()
+    for lat in lats:
+        lat.close()
+
+
+def test_tuner_picks_a_candidate_and_keeps_results():
+    beds, forces = _beds(5, seed=4)
+    lats = _lattices(beds)
+    a = BatchedState(lats, "f32s")
+    block, cpt, ms = a.tune(3, WP, WM, forces)
+    assert block in (128, 256, 512) and cpt in (1, 2, 4)
+    assert len(ms) == 9 and min(ms) > 0
+    taken = 9 * 4
+    b = BatchedState(lats, "f32s")
+    b.configure(256, 1, False)
+    b.step(taken, WP, WM, forces)
+    np.testing.assert_array_equal(a.get_pdfs().cpu().numpy(), b.get_pdfs().cpu().numpy())
+    a.close()
+    b.close()
+    for lat in lats:
+        lat.close()
+
+
+def test_full_batch_of_256_beds_sampled():
+    """The 256-bed workload (cube sides uniform in {24..96}, radii in [3, 8],
+    forces in [1e-7, 1e-5] along z), FP32 shifted storage, 1000 steps as one
+    graph: per-bed flux of 8 sampled beds equals their separate runs."""
+    beds, fz = inputs.batch_beds(256, 0)
+    forces = [(0.0, 0.0, float(f)) for f in fz]
+    lats = _lattices(beds)
+    bs = BatchedState(lats, "f32s")
+    bs.configure(256, 2, True)
+    bs.step(1000, WP, WM, forces)
+    mass, flux = bs.reduce_flux(2)
+    assert bs.n_fluid == sum(b.n_fluid for b in beds)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(256, 8, replace=False):
+        st = LBMState(lats[i], "f32s")
+        st.step(1000, WP, WM, forces[i])
+        assert st.reduce_flux(2) == (mass[i], flux[i])
+        st.close()
+    bs.close()
+    for lat in lats:
+        lat.close()
