@@ -271,6 +271,18 @@ int lbm_batch_tune(lbm_state* st, int32_t steps_per_candidate, double omega_plus
                    double omega_minus, const double* forces, int32_t* block_out,
                    int32_t* cpt_out, float* ms_out);
 
+/* ---- halo exchange of a chunked list ------------------------------------
+ * The flow solver cuts the fluid-cell list into equal chunks, one per rank,
+ * and before every step each rank receives the PDFs of its remote links
+ * into ghost cells that follow its own PDFs (Sec. 2; Fig. 1c).  This is the
+ * pack side of that exchange: dst_dev[i] = src_dev[slots_dev[i]] for
+ * i < count, elements of elem_bytes in {2, 4, 8}; slots_dev is a device
+ * int64 array.  On one device dst_dev may point into the receiving chunk's
+ * ghost run directly.  Asynchronous on `stream`.
+ */
+int lbm_halo_gather(const void* src_dev, const int64_t* slots_dev, int64_t count, void* dst_dev,
+                    int32_t elem_bytes, void* stream);
+
 /* ---- adjoint (reverse mode) ---------------------------------------------
  * Gradients of J = (1/N) sum_n u_axis,n, the mean axial velocity of the
  * collision of step K, with respect to the body force F and the per-cell

@@ -71,6 +71,8 @@ def _load():
             lib.oracle_adjoint.argtypes = [vp, vp, u32, d, d, vp, vp, i32, i32, vp, vp, vp, vp,
                                            vp]
             lib.oracle_adjoint.restype = ctypes.c_int
+            lib.oracle_sparse_step.argtypes = [vp, vp, vp, i64, vp, vp, d, d]
+            lib.oracle_sparse_step.restype = None
             _lib = lib
     return _lib
 
@@ -189,3 +191,16 @@ def to_sparse(dense, cells) -> np.ndarray:
     """Gather a dense [..., nz, ny, nx] field onto the fluid-cell list."""
     lead = dense.shape[:-3]
     return dense.reshape(lead + (-1,))[..., cells]
+
+
+def sparse_step(f_src, adj, n: int, F, omega_p: float, omega_m: float, alpha=None):
+    """One step on a sparse list: f_src is 1-D (19 n own PDFs, possibly
+    followed by ghosts), adj [18, n] indexes it; returns f_dst [19 * n]."""
+    f_src = np.ascontiguousarray(f_src, np.float64).ravel()
+    adj = np.ascontiguousarray(adj, np.int32)
+    F = np.ascontiguousarray(F, np.float64)
+    a = None if alpha is None else np.ascontiguousarray(alpha, np.float64)
+    out = np.empty(19 * int(n))
+    _load().oracle_sparse_step(_p(f_src), _p(out), _p(adj), int(n), _p(F), _p(a),
+                               float(omega_p), float(omega_m))
+    return out

@@ -498,3 +498,22 @@ void oracle_keys(int32_t kind, const int32_t dims[3], const int32_t block[3], ui
         keys[x + (int64_t)dims[0] * (y + (int64_t)dims[1] * z)] =
             oracle_key(kind, dims, block, x, y, z);
 }
+
+/* One time step on the sparse representation (Sec. 2 and Sec. 7): each of
+ * the n cells pulls g_0 = f_src[i] and g_q = f_src[adj[(q-1)*n + i]], then
+ * collides; f_dst[q*n + i] = f*_q.  f_src may be longer than 19 n (for
+ * example a rank's ghost cells after its own PDFs); adj entries index it.
+ * alpha: per-cell damping [n] or NULL.  Used to emulate the ranks of a
+ * chunked run; pinned against the dense pull solver by the tests. */
+void oracle_sparse_step(const double* f_src, double* f_dst, const int32_t* adj, int64_t n,
+                        const double F[3], const double* alpha, double omega_p,
+                        double omega_m) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double g[19], fo[19];
+    g[0] = f_src[i];
+    for (int q = 1; q < 19; ++q) g[q] = f_src[adj[(int64_t)(q - 1) * n + i]];
+    oracle_collide(g, F, alpha ? alpha[i] : 0.0, omega_p, omega_m, fo, NULL, NULL);
+    for (int q = 0; q < 19; ++q) f_dst[(int64_t)q * n + i] = fo[q];
+  }
+}

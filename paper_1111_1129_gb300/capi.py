@@ -49,6 +49,7 @@ SIGNATURES = {
     "lbm_batch_layout": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "lbm_batch_config": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
     "lbm_batch_tune": (ctypes.c_int, [_vp, _i32, _d, _d, _vp, _vp, _vp, _vp]),
+    "lbm_halo_gather": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i32, _vp]),
     "lbm_adjoint_create": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
     "lbm_adjoint_forward": (ctypes.c_int, [_vp, _d, _d, _vp, _i32, _vp]),
     "lbm_adjoint_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -226,6 +227,12 @@ def lbm_batch_tune(state: int, steps_per_candidate: int, omega_plus: float, omeg
                                  float(omega_minus), _forces(forces), ctypes.byref(b),
                                  ctypes.byref(c), ms))
     return b.value, c.value, list(ms)
+
+
+def lbm_halo_gather(src_dev: int, slots_dev: int, count: int, dst_dev: int, elem_bytes: int,
+                    stream: int) -> None:
+    _check(load().lbm_halo_gather(src_dev, slots_dev, int(count), dst_dev, int(elem_bytes),
+                                  stream))
 
 
 def lbm_adjoint_create(state: int, n_steps: int, stride: int = 0) -> int:
