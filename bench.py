@@ -35,7 +35,8 @@ sys.path.insert(0, ROOT)
 WP = 1.0 / 0.8
 FORCE = (1e-6, 0.0, 0.0)
 AXIS = 0
-BYTES_PER_LUP = {"f64": 19 * 8 * 2 + 18 * 4, "f32": 19 * 4 * 2 + 18 * 4,
+BYTES_PER_LUP = {"f64": 19 * 8 * 2 + 18 * 4, "f64x": 19 * 8 * 2 + 18 * 4,
+                 "f32": 19 * 4 * 2 + 18 * 4,
                  "f32s": 19 * 4 * 2 + 18 * 4, "f16s": 19 * 2 * 2 + 18 * 4,
                  "bf16s": 19 * 2 * 2 + 18 * 4}
 WORKLOADS = {
@@ -329,7 +330,7 @@ def _extras(lat, bed, wm, args):
             l2.close()
     out["f64_by_ordering_mflups"] = orders
     forms = {}
-    for prec, k in (("f32", 0), ("f32s", 0), ("f16s", 24), ("bf16s", 24)):
+    for prec, k in (("f64x", 0), ("f32", 0), ("f32s", 0), ("f16s", 24), ("bf16s", 24)):
         forms[prec] = timed(lat, prec, args.extra_steps, k)
     out["by_storage_mflups"] = forms
     return out
@@ -354,7 +355,7 @@ def run_precision_study(args):
     k16 = shifted_scale_exp(deviation_bound(FORCE[0], 61.0, WP))
     rows = {}
     ref_u = ref_flux = None
-    for prec in ("f64", "f32s", "f16s", "f32", "bf16s"):
+    for prec in ("f64", "f64x", "f32s", "f16s", "f32", "bf16s"):
         st = LBMState(lat, prec, k16)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -450,6 +451,72 @@ def run_batch_study(args):
     return 0
 
 
+def _interface_metrics_gpu(adj, n, p):
+    """Neighbour partitions and remote links per chunk of p equal chunks
+    (Fig. 7 metrics), on the GPU for large lists."""
+    import torch
+
+    q, r = divmod(n, p)
+    k = torch.arange(p + 1, device="cuda", dtype=torch.int64)
+    bounds = k * q + torch.minimum(k, torch.tensor(r, device="cuda"))
+    cell_owner = torch.searchsorted(bounds, torch.arange(n, device="cuda"), right=True) - 1
+    links = torch.zeros(p, dtype=torch.int64, device="cuda")
+    pairs = []
+    for i in range(18):
+        m = adj[i].to(torch.int64) % n
+        so = torch.searchsorted(bounds, m, right=True) - 1
+        remote = so != cell_owner
+        links += torch.bincount(cell_owner[remote], minlength=p)
+        pairs.append(torch.unique(cell_owner[remote] * p + so[remote]))
+    uniq = torch.unique(torch.cat(pairs))
+    nb = torch.bincount(uniq // p, minlength=p)
+    return nb.float(), links.float()
+
+
+def run_ordering_study(args):
+    """MFLUP/s of the HBM-bound storage forms and the chunk-interface
+    metrics as functions of the numbering scheme (lexicographic with
+    blocking factor b = 1..128, Z curve 1-bit and 2-bit) on the
+    1024x256x256 bed: the GB300 counterpart of Sec. 7's Fig. 4 and Fig. 7."""
+    import torch
+
+    from paper_1111_1129_gb300 import LBMState, SparseLattice, capi, inputs, omega_minus
+
+    capi.load()
+    wm = omega_minus(WP)
+    bed = inputs.bed_large(0)
+    flags = torch.from_numpy(bed.flags).cuda()
+    rows = []
+    orders = [("lex", (1, 1, 1))] + [("blocked", (b, b, b)) for b in (2, 4, 8, 16, 32, 64, 128)] + [
+        ("morton1", (1, 1, 1)), ("morton2", (1, 1, 1))]
+    for name, block in orders:
+        lat = SparseLattice(flags, name, block, bed.periodic)
+        row = {"ordering": name if name != "blocked" else f"blocked {block[0]}"}
+        for prec in args.study_forms.split(","):
+            st = LBMState(lat, prec, 24)
+            st.step(3, WP, wm, FORCE)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st.step(args.extra_steps, WP, wm, FORCE)
+            e1.record()
+            torch.cuda.synchronize()
+            row[f"{prec}_mflups"] = lat.n * args.extra_steps / (e0.elapsed_time(e1) * 1e-3) / 1e6
+            st.close()
+        adj = torch.as_tensor(lat.adjacency())
+        for p in (64, 1024):
+            nb, links = _interface_metrics_gpu(adj, lat.n, p)
+            row[f"P{p}_neighbours_mean"] = nb.mean().item()
+            row[f"P{p}_neighbours_max"] = nb.max().item()
+            row[f"P{p}_remote_links_mean"] = links.mean().item()
+        del adj
+        rows.append(row)
+        lat.close()
+    print(json.dumps({"study": "ordering", "workload": WORKLOADS["large"][0],
+                      "steps_each": args.extra_steps, "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,6 +537,9 @@ def main():
     ap.add_argument("--batch-study", action="store_true",
                     help="run the 256-bed batching study instead of the benchmark")
     ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--ordering-study", action="store_true",
+                    help="run the numbering-scheme study instead of the benchmark")
+    ap.add_argument("--study-forms", default="f64,f32s,f16s")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -477,6 +547,8 @@ def main():
         return run_precision_study(args)
     if args.batch_study:
         return run_batch_study(args)
+    if args.ordering_study:
+        return run_ordering_study(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -89,6 +89,10 @@ typedef struct lbm_ordering {
 #define LBM_F32S 2  /* f - w_q in FP32, FP32 arithmetic */
 #define LBM_F16S 3  /* (f - w_q) * 2^k in FP16, FP32 arithmetic */
 #define LBM_BF16S 4 /* (f - w_q) * 2^k in BF16, FP32 arithmetic */
+#define LBM_F64X 5  /* f in FP64; the sweep computes f - w_q exactly in 64-bit
+                       fixed point (unit 2^-58) instead of FP64 instructions,
+                       conserves mass exactly and agrees with LBM_F64 to FP64
+                       round-off; other operations run as LBM_F64 */
 
 typedef struct lbm_sparse lbm_sparse;
 typedef struct lbm_state lbm_state;

@@ -18,10 +18,11 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm_gb300.so")
-SOURCES = ["assembly.cu", "sweep.cu", "adjoint.cu", "batch.cu", "halo.cu", "capi.cu"]
+SOURCES = ["assembly.cu", "sweep.cu", "sweep_fx.cu", "adjoint.cu", "batch.cu", "halo.cu",
+           "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "-I" + INCLUDE]
+         "-I" + INCLUDE] + os.environ.get("LBM_NVCC_FLAGS", "").split()
 
 
 def nvcc() -> str:

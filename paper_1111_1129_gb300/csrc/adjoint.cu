@@ -365,6 +365,7 @@ int run_backward(lbm_adjoint* ad, double* dJdf0) {
 #define LBM_ADJ_DISPATCH(prec, fn, ...)                      \
   switch (prec) {                                            \
     case LBM_F64: return fn<LBM_F64>(__VA_ARGS__);           \
+    case LBM_F64X: return fn<LBM_F64X>(__VA_ARGS__);         \
     case LBM_F32: return fn<LBM_F32>(__VA_ARGS__);           \
     case LBM_F32S: return fn<LBM_F32S>(__VA_ARGS__);         \
     case LBM_F16S: return fn<LBM_F16S>(__VA_ARGS__);         \

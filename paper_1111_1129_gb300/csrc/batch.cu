@@ -227,6 +227,7 @@ size_t force_bytes() {
 #define LBM_BATCH_DISPATCH(prec, fn, ...)                    \
   switch (prec) {                                            \
     case LBM_F64: return fn<LBM_F64>(__VA_ARGS__);           \
+    case LBM_F64X: return fn<LBM_F64X>(__VA_ARGS__);         \
     case LBM_F32: return fn<LBM_F32>(__VA_ARGS__);           \
     case LBM_F32S: return fn<LBM_F32S>(__VA_ARGS__);         \
     case LBM_F16S: return fn<LBM_F16S>(__VA_ARGS__);         \
@@ -257,7 +258,7 @@ int batch_reduce(lbm_state* st, int32_t axis, double* mass_out, double* flux_out
   } else {
     for (int i = 0; i < 4 * b->n_beds; ++i) b->h_red[i] = 0.0;
   }
-  const bool shifted = st->precision != LBM_F64 && st->precision != LBM_F32;
+  const bool shifted = is_shifted(st->precision);
   for (int i = 0; i < b->n_beds; ++i) {
     const double cnt = (double)b->h_count[i];
     const double mass = shifted ? cnt + b->h_red[4 * i] : b->h_red[4 * i];

@@ -206,6 +206,9 @@ void free_sparse(lbm_sparse* sp);
 void free_adjoint(lbm_adjoint* ad);
 size_t storage_bytes(int prec);   // bytes per stored PDF of a precision form
 size_t compute_bytes(int prec);   // bytes of the arithmetic type of a form
+bool is_shifted(int prec);        // stores f - w_q rather than f
+// Fixed-point FP64-storage sweep (sweep_fx.cu), undamped.
+int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3]);
 bool valid_state(const lbm_state* st);
 // Records `ev` on `stream` and polls it with a wall-clock limit (<= 0: the
 // library default); LBM_ETIMEOUT if the work is still running then.

@@ -23,6 +23,12 @@ struct Form<LBM_F64> {
   static constexpr bool kShifted = false;
 };
 template <>
+struct Form<LBM_F64X> {  // FP64 storage; the sweep itself runs in fixed point
+  using S = double;
+  using C = double;
+  static constexpr bool kShifted = false;
+};
+template <>
 struct Form<LBM_F32> {
   using S = float;
   using C = float;

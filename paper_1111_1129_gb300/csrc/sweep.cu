@@ -71,12 +71,13 @@ __global__ void set_alpha_kernel(C* dst, const double* a, int32_t n) {
 
 size_t storage_bytes(int prec) {
   switch (prec) {
-    case LBM_F64: return 8;
+    case LBM_F64: case LBM_F64X: return 8;
     case LBM_F32: case LBM_F32S: return 4;
     default: return 2;
   }
 }
-size_t compute_bytes(int prec) { return prec == LBM_F64 ? 8 : 4; }
+size_t compute_bytes(int prec) { return (prec == LBM_F64 || prec == LBM_F64X) ? 8 : 4; }
+bool is_shifted(int prec) { return prec == LBM_F32S || prec == LBM_F16S || prec == LBM_BF16S; }
 
 static double g_timeout_s = 600.0;
 
@@ -106,6 +107,9 @@ int launch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const dou
   using C = typename Form<PREC>::C;
   const int32_t n = (int32_t)st->sp->n;
   const cudaStream_t stream = st->sp->stream;
+  if constexpr (PREC == LBM_F64X) {
+    if (!st->alpha) return launch_steps_fx(st, n_steps, wp, wm, F);
+  }
   const Coef<C> k = make_coef<C>(wp, wm, F, st->scale_exp);
   const unsigned grid = (unsigned)st->nblocks;
   const C* alpha = (const C*)st->alpha;
@@ -170,6 +174,7 @@ int launch_get(const lbm_state* st, double* f) {
 #define LBM_DISPATCH(prec, fn, ...)                          \
   switch (prec) {                                            \
     case LBM_F64: return fn<LBM_F64>(__VA_ARGS__);           \
+    case LBM_F64X: return fn<LBM_F64X>(__VA_ARGS__);         \
     case LBM_F32: return fn<LBM_F32>(__VA_ARGS__);           \
     case LBM_F32S: return fn<LBM_F32S>(__VA_ARGS__);         \
     case LBM_F16S: return fn<LBM_F16S>(__VA_ARGS__);         \
@@ -212,7 +217,7 @@ extern "C" int lbm_state_create(const lbm_sparse* sp, int32_t precision, int32_t
   if (!out) return fail(LBM_EINVAL, "out is NULL");
   *out = nullptr;
   if (!sp || sp->magic != kMagicSparse) return fail(LBM_EINVAL, "not a sparse handle");
-  if (precision < LBM_F64 || precision > LBM_BF16S)
+  if (precision < LBM_F64 || precision > LBM_F64X)
     return fail(LBM_EINVAL, "unknown precision %d", precision);
   if ((precision == LBM_F16S || precision == LBM_BF16S) && (scale_exp < 0 || scale_exp > 40))
     return fail(LBM_EINVAL, "scale_exp %d outside [0, 40]", scale_exp);
@@ -343,7 +348,7 @@ extern "C" int lbm_reduce_flux(lbm_state* st, int32_t axis, double* mass_out, do
   } else {
     for (int j = 0; j < 4; ++j) st->red_host[j] = 0.0;
   }
-  const bool shifted = st->precision != LBM_F64 && st->precision != LBM_F32;
+  const bool shifted = is_shifted(st->precision);
   const double mass = shifted ? (double)n + st->red_host[0] : st->red_host[0];
   const double flux = n > 0 ? st->red_host[1 + axis] / (double)n : 0.0;
   if (!std::isfinite(mass) || !std::isfinite(flux))

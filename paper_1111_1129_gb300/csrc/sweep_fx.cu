@@ -1,0 +1,223 @@
+// FP64-storage sweep in exact 64-bit fixed point (precision form LBM_F64X).
+//
+// GB300 issues FP64 at about 1/64 of its FP32 rate, so a TRT update in
+// IEEE FP64 arithmetic (~140 FP64 instructions) is bound by the FP64 pipe
+// at ~4.3 GLUP/s, a quarter of what HBM could feed.  This kernel keeps the
+// PDFs in FP64 but computes without FP64 instructions:
+//
+//  * Every f_q lies near its weight w_q (1/3, 1/18, 1/36), inside the same
+//    binary range [2^E_q, 2^(E_q+1)).  There the difference of the raw
+//    64-bit patterns, bits(f_q) - bits(w_q), is the exact deviation
+//    f_q - w_q in units of the range's ulp 2^(E_q-52).  Shifting it to the
+//    common unit U = 2^-58 gives an exact int64 X_q; the store converts
+//    back the same way.  No FP64 conversion is needed on this path.
+//  * Pair sums/differences, rho - 1 and j are then exact integer sums.
+//  * Products with the relaxation constants use 64x64 -> high-64 integer
+//    multiplies with the constants scaled by 2^63 (relative precision
+//    2^-62).  The quadratic velocity terms, ~u^2 ~ 1e-10 of f, are done in
+//    FP32 (absolute error ~1e-17) and rounded to units.
+//  * After rounding to the storage units, the rest population takes the
+//    remainder rho - 1 - sum_{q>0} X*_q (and a diagonal population the last
+//    sub-unit part), so every collision conserves the stored mass exactly.
+//
+// A cell with any PDF outside its range (fast flow, random test states,
+// NaN) takes the IEEE FP64 collision instead, and an output that leaves its
+// range is written through FP64; both are exact to FP64 round-off.  The
+// update is the TRT update of the FP64 form (same pair formulation), with
+// errors below FP64 round-off of f.
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+namespace {
+
+struct FxCoef {
+  int64_t hp, hm, w1p, a1;  // (1-w+)/2, (1-w-)/2, w+/18, w-/6, each * 2^63
+  int64_t q1;               // w+/36 (quadratic terms) * 2^63
+  int64_t hF[3];            // F/2 in units U
+  int64_t bF1[3];           // (1 - w-/2) F / 6 in units U
+};
+
+// (a * b) / 2^58 for |a|, |b| < 2^52, from three 32x32 -> 64 products:
+// with a = ah 2^29 + al (0 <= al < 2^29), a b / 2^58 = ah bh +
+// (ah bl + al bh) / 2^29 + al bl / 2^58; the last term (< 1) and the floor
+// of the middle one make it exact to within 2 units.
+__device__ __forceinline__ int64_t uprod(int64_t a, int64_t b) {
+  const int32_t ah = (int32_t)(a >> 29), bh = (int32_t)(b >> 29);
+  const int32_t al = (int32_t)(a & 0x1FFFFFFF), bl = (int32_t)(b & 0x1FFFFFFF);
+  return (int64_t)ah * bh + (((int64_t)ah * bl + (int64_t)al * bh) >> 29);
+}
+
+constexpr int64_t kW0Bits = 0x3FD5555555555555LL;  // 1/3
+constexpr int64_t kW1Bits = 0x3FAC71C71C71C71CLL;  // 1/18
+constexpr int64_t kW2Bits = 0x3F9C71C71C71C71CLL;  // 1/36
+
+__device__ __forceinline__ int64_t wbits(int q) { return q == 0 ? kW0Bits : (q <= 6 ? kW1Bits : kW2Bits); }
+__device__ __forceinline__ int64_t wexp(int q) { return q == 0 ? 0x3FD : (q <= 6 ? 0x3FA : 0x3F9); }
+__device__ __forceinline__ int wshift(int q) { return q == 0 ? 4 : (q <= 6 ? 1 : 0); }
+
+// x * c for a constant c = c63 / 2^63 (|c| < 1/2), |x| < 2^59: floor.
+__device__ __forceinline__ int64_t fxmul(int64_t x, int64_t c63) { return __mul64hi(2 * x, c63); }
+
+// Resident blocks of 256 threads per SM the register budget is fitted to:
+// 3 (80 registers) measured 13.2 GLUP/s on the 1024x256x256 bed against
+// 11.5 for 2 (120 registers) and 12.6 for 4 (64 registers, heavy spills).
+#ifndef LBM_FX_MIN_BLOCKS
+#define LBM_FX_MIN_BLOCKS 3
+#endif
+
+template <bool REDUCE>
+__global__ void __launch_bounds__(kSweepThreads, LBM_FX_MIN_BLOCKS)
+    sweep_fx_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                    const int32_t* __restrict__ adj, int32_t n, FxCoef k, Coef<double> kd,
+                    double* __restrict__ partials) {
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < n) {
+    int32_t idx[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) idx[q] = __ldcs(adj + q * n + i);
+    int64_t b[19];
+    b[0] = __double_as_longlong(__ldg(src + i));
+#pragma unroll
+    for (int q = 1; q < 19; ++q) b[q] = __double_as_longlong(__ldg(src + idx[q - 1]));
+    bool fast = true;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) fast &= (b[q] >> 52) == wexp(q);
+    int64_t X[19], S[9], D[9], drho = 0, ux = 0, uy = 0, uz = 0;
+    if (fast) {
+#pragma unroll
+      for (int q = 0; q < 19; ++q) X[q] = (b[q] - wbits(q)) << wshift(q);
+#pragma unroll
+      for (int p = 0; p < 9; ++p) {
+        S[p] = X[2 * p + 1] + X[2 * p + 2];
+        D[p] = X[2 * p + 1] - X[2 * p + 2];
+      }
+      drho = X[0] + (((S[0] + S[1]) + (S[2] + S[3])) + ((S[4] + S[5]) + (S[6] + S[7])) + S[8]);
+      ux = (((D[0] + D[3]) + (D[4] + D[5])) + D[6]) + k.hF[0];
+      uy = (((D[1] + D[3]) - (D[4] - D[7])) + D[8]) + k.hF[1];
+      uz = (((D[2] + D[5]) - (D[6] - D[7])) - D[8]) + k.hF[2];
+      // exact quadratic terms need |u| < 2^-6 (2^52 units)
+      const int64_t lim = 1LL << 52;
+      fast = ux > -lim && ux < lim && uy > -lim && uy < lim && uz > -lim && uz < lim;
+    }
+    if (fast) {
+      const int64_t V1x = fxmul(ux, k.a1) + k.bF1[0];
+      const int64_t V1y = fxmul(uy, k.a1) + k.bF1[1];
+      const int64_t V1z = fxmul(uz, k.a1) + k.bF1[2];
+      const int64_t V2x = V1x >> 1, V2y = V1y >> 1, V2z = V1z >> 1;
+      // Quadratic terms w+ w_p (4.5 (c.u)^2 - 1.5 u.u) = (w+ w_p / 2)
+      // (9 (c.u)^2 - 3 u.u): with v = (w+/36) u, the products
+      // T_ab = v_a u_b carry the class-1 factor (w+ w1 / 2 = w+/36), so
+      // quad_1 = 9 T_aa - 3 T_tr and quad_2 = that expression / 2 for the
+      // diagonal (c.u)^2 = T_aa + T_bb +- 2 T_ab.
+      const int64_t vx = fxmul(ux, k.q1), vy = fxmul(uy, k.q1), vz = fxmul(uz, k.q1);
+      const int64_t Txx = uprod(vx, ux), Tyy = uprod(vy, uy), Tzz = uprod(vz, uz);
+      const int64_t Txy2 = 2 * uprod(vx, uy), Txz2 = 2 * uprod(vx, uz), Tyz2 = 2 * uprod(vy, uz);
+      const int64_t Ttr3 = 3 * (Txx + Tyy + Tzz);
+      const int64_t R1 = fxmul(drho, k.w1p);
+      const int64_t R2 = R1 >> 1;
+      int64_t out[19];
+#define LBM_FX_PAIR(P, QUAD, R, VX)                                         \
+  {                                                                         \
+    const int64_t P_ = fxmul(S[P], k.hp) + R + (QUAD);                      \
+    const int64_t Q_ = fxmul(D[P], k.hm) + (VX);                            \
+    out[2 * P + 1] = P_ + Q_;                                               \
+    out[2 * P + 2] = P_ - Q_;                                               \
+  }
+      LBM_FX_PAIR(0, 9 * Txx - Ttr3, R1, V1x)
+      LBM_FX_PAIR(1, 9 * Tyy - Ttr3, R1, V1y)
+      LBM_FX_PAIR(2, 9 * Tzz - Ttr3, R1, V1z)
+      LBM_FX_PAIR(3, (9 * (Txx + Tyy + Txy2) - Ttr3) >> 1, R2, V2x + V2y)
+      LBM_FX_PAIR(4, (9 * (Txx + Tyy - Txy2) - Ttr3) >> 1, R2, V2x - V2y)
+      LBM_FX_PAIR(5, (9 * (Txx + Tzz + Txz2) - Ttr3) >> 1, R2, V2x + V2z)
+      LBM_FX_PAIR(6, (9 * (Txx + Tzz - Txz2) - Ttr3) >> 1, R2, V2x - V2z)
+      LBM_FX_PAIR(7, (9 * (Tyy + Tzz + Tyz2) - Ttr3) >> 1, R2, V2y + V2z)
+      LBM_FX_PAIR(8, (9 * (Tyy + Tzz - Tyz2) - Ttr3) >> 1, R2, V2y - V2z)
+#undef LBM_FX_PAIR
+      // Round the moving populations to their storage units (2^-57 axis,
+      // 2^-58 diagonal); the rest population takes the remainder rounded to
+      // its unit 2^-54, and the last -8..7 units go to a diagonal
+      // population, so the stored deviations sum exactly to drho: every
+      // step conserves the stored mass bit for bit.
+      int64_t d[19];
+      int64_t stored = 0;
+#pragma unroll
+      for (int q = 1; q < 19; ++q) {
+        const int s = wshift(q);
+        d[q] = s ? (out[q] + (1LL << (s - 1))) >> s : out[q];
+        stored += d[q] << s;
+      }
+      const int64_t rem = drho - stored;
+      d[0] = (rem + 8) >> 4;
+      d[7] += rem - (d[0] << 4);
+#pragma unroll
+      for (int q = 0; q < 19; ++q) {
+        const int64_t bits = wbits(q) + d[q];
+        double v;
+        if ((bits >> 52) == wexp(q))
+          v = __longlong_as_double(bits);
+        else
+          v = weight(q) + (double)(d[q] << wshift(q)) * 0x1p-58;
+        __stcs(dst + q * n + i, v);
+      }
+      if (REDUCE) {
+        red[0] = 1.0 + (double)drho * 0x1p-58;
+        red[1] = (double)ux * 0x1p-58;
+        red[2] = (double)uy * 0x1p-58;
+        red[3] = (double)uz * 0x1p-58;
+      }
+    } else {
+      double g[19];
+#pragma unroll
+      for (int q = 0; q < 19; ++q) g[q] = __longlong_as_double(b[q]);
+      double rho, u[3];
+      collide<double, false>(g, kd, 0.0, rho, u);
+#pragma unroll
+      for (int q = 0; q < 19; ++q) __stcs(dst + q * n + i, g[q]);
+      if (REDUCE) {
+        red[0] = rho;
+        red[1] = u[0];
+        red[2] = u[1];
+        red[3] = u[2];
+      }
+    }
+  }
+  if (REDUCE) block_sum4(red, partials + 4 * (int64_t)blockIdx.x);
+}
+
+int64_t c63(double c) { return (int64_t)std::llround(c * 0x1p63); }
+int64_t units(double v) { return (int64_t)std::llround(v * 0x1p58); }
+
+}  // namespace
+
+int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3]) {
+  const int32_t n = (int32_t)st->sp->n;
+  const cudaStream_t stream = st->sp->stream;
+  FxCoef k{};
+  k.hp = c63(0.5 * (1.0 - wp));
+  k.hm = c63(0.5 * (1.0 - wm));
+  k.w1p = c63(wp / 18.0);
+  k.a1 = c63(wm / 6.0);
+  for (int d = 0; d < 3; ++d) {
+    k.hF[d] = units(0.5 * F[d]);
+    k.bF1[d] = units((1.0 - 0.5 * wm) * F[d] / 6.0);
+  }
+  k.q1 = c63(wp / 36.0);
+  const Coef<double> kd = make_coef<double>(wp, wm, F, 0);
+  const unsigned grid = (unsigned)st->nblocks;
+  for (int32_t t = 0; t < n_steps; ++t) {
+    const double* src = (const double*)st->buf[st->cur];
+    double* dst = (double*)st->buf[st->cur ^ 1];
+    if (n > 0) {
+      if (t == n_steps - 1)
+        sweep_fx_kernel<true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials);
+      else
+        sweep_fx_kernel<false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials);
+    }
+    st->cur ^= 1;
+  }
+  LBM_CUDA_TRY(cudaGetLastError());
+  return LBM_OK;
+}
+
+}  // namespace lbm

@@ -16,8 +16,8 @@ from . import capi
 ORDERINGS = {"lex": capi.LBM_ORDER_LEX, "blocked": capi.LBM_ORDER_BLOCKED,
              "morton1": capi.LBM_ORDER_MORTON1, "morton2": capi.LBM_ORDER_MORTON2}
 PRECISIONS = {"f64": capi.LBM_F64, "f32": capi.LBM_F32, "f32s": capi.LBM_F32S,
-              "f16s": capi.LBM_F16S, "bf16s": capi.LBM_BF16S}
-STORAGE_BYTES = {"f64": 8, "f32": 4, "f32s": 4, "f16s": 2, "bf16s": 2}
+              "f16s": capi.LBM_F16S, "bf16s": capi.LBM_BF16S, "f64x": capi.LBM_F64X}
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f32s": 4, "f16s": 2, "bf16s": 2, "f64x": 8}
 
 
 def omega_minus(omega_plus: float, magic: float = 3.0 / 16.0) -> float:
