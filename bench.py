@@ -3,7 +3,11 @@
 Workload: the 1024x256x256 packed bed (tube of diameter 250 along x,
 spheres of radius 8 by seeded random sequential addition, periodic in x,
 ~33 M fluid cells), body force 1e-6 along x, omega+ = 1/0.8, Lambda = 3/16,
-rest initial state, FP64 PDFs, 8^3-blocked lexicographic order.
+rest initial state, FP64 PDFs, 8^3-blocked lexicographic order.  The
+default form is f64x: FP64 storage with the update computed in exact 64-bit
+fixed point (results equal IEEE FP64 to round-off); --precision f64 times
+the IEEE-FP64-arithmetic kernel, which GB300's FP64 rate caps near 4.3
+GLUP/s.
 
 One "step" is one time step of the hot path: pull through the adjacency
 list, TRT collision, streaming store (one kernel launch per step), with the
@@ -39,6 +43,21 @@ BYTES_PER_LUP = {"f64": 19 * 8 * 2 + 18 * 4, "f64x": 19 * 8 * 2 + 18 * 4,
                  "f32": 19 * 4 * 2 + 18 * 4,
                  "f32s": 19 * 4 * 2 + 18 * 4, "f16s": 19 * 2 * 2 + 18 * 4,
                  "bf16s": 19 * 2 * 2 + 18 * 4}
+# DRAM bytes (read + write) per fluid update measured by ncu on the
+# 256x128x128 bed (profiles/sweep_*_bed256x128x128_ncu.md); the roofline's
+# `traffic` scales them to the benchmark's cells.  Reset an entry to None
+# when its kernel changes.
+MEASURED_DRAM_BYTES_PER_LUP = {"f64x": 351.2, "f64": 347.8}
+STORAGE = {"f64": "f64", "f64x": "f64", "f32": "f32", "f32s": "f32 (f - w)",
+           "f16s": "f16 ((f - w) 2^k)", "bf16s": "bf16 ((f - w) 2^k)"}
+ARITHMETIC = {"f64": "f64", "f64x": "int64", "f32": "f32", "f32s": "f32", "f16s": "f32",
+              "bf16s": "f32"}
+ARITHMETIC_NOTE = {
+    "f64": "IEEE FP64",
+    "f64x": "exact 64-bit fixed point on f - w (unit 2^-58); results agree with IEEE FP64 to "
+            "round-off (parity 1e-12 vs the oracle) and conserve the stored mass exactly; "
+            "cells outside the fast range use IEEE FP64",
+    "f32": "FP32", "f32s": "FP32", "f16s": "FP32", "bf16s": "FP32"}
 WORKLOADS = {
     "large": ("packed bed 1024x256x256, tube D=250 along x, spheres r=8, seed 0", "bed_large"),
     "medium": ("packed bed 256x128x128, tube D=122 along x, spheres r=8, seed 0", "bed_medium"),
@@ -149,14 +168,14 @@ def run_reference(args):
     bed = getattr(inputs, WORKLOADS[args.workload][1])(0)
     for _ in range(args.warmup):
         _oracle_sample(bed, 0.5, max_steps=1)
-    t0 = time.perf_counter()
     lups = 0.0
+    dt = 0.0          # the oracle's own time steps; its per-sample set-up is not counted
     samples = []
     for _ in range(args.steps):
-        mflups, steps, n_fluid, cores, dt = _oracle_sample(bed, 3.0)
+        mflups, steps, n_fluid, cores, t = _oracle_sample(bed, 3.0)
         lups += n_fluid * steps
+        dt += t
         samples.append(steps)
-    dt = time.perf_counter() - t0
     value = lups / dt / 1e6
     line = {
         "impl": "reference", "metric": "MFLUP/s", "value": value, "unit": "MFLUP/s",
@@ -268,18 +287,22 @@ def run_ours(args):
         "metric": "MFLUP/s", "value": value, "unit": "MFLUP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": args.precision, "data": "synthetic",
+        "dtype": ARITHMETIC[args.precision], "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][0], "fluid_cells_per_gpu": n, "ordering": f"{args.ordering}"
                    + (" 8^3" if args.ordering == "blocked" else ""),
-                   "precision": args.precision, "force": list(FORCE),
+                   "precision": args.precision, "storage": STORAGE[args.precision],
+                   "arithmetic": ARITHMETIC_NOTE[args.precision], "force": list(FORCE),
                    "omega_plus": WP, "omega_minus": wm,
                    "l2": "inputs larger than L2 (PDFs+adjacency ~%.1f GB)" % (
                        (2 * 19 * (bpl - 72) / 38 + 72) * n / 1e9),
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (MEASURED_DRAM_BYTES_PER_LUP[args.precision] * n
+                                 if MEASURED_DRAM_BYTES_PER_LUP.get(args.precision) else None),
                      "bytes_per_lup": bpl, "peak_kind": peak_kind,
-                     "kernel": f"sweep_kernel<{args.precision}>"},
+                     "kernel": "sweep_fx_kernel" if args.precision == "f64x"
+                     else f"sweep_kernel<{args.precision}>"},
         "e2e": {"value": e2e_value, "unit": "MFLUP/s",
                 "h2d_bytes_per_step": (bed.flags.nbytes + 24) / args.steps,
                 "d2h_bytes_per_step": 32 / args.steps},
@@ -325,13 +348,16 @@ def _extras(lat, bed, wm, args):
             l2 = lat
         else:
             l2 = SparseLattice(torch.from_numpy(bed.flags).cuda(), name, (8, 8, 8), bed.periodic)
-        orders[name + (" 8^3" if name == "blocked" else "")] = timed(l2, "f64", args.extra_steps)
+        orders[name + (" 8^3" if name == "blocked" else "")] = timed(l2, args.precision,
+                                                                    args.extra_steps)
         if l2 is not lat:
             l2.close()
-    out["f64_by_ordering_mflups"] = orders
+    out[f"{args.precision}_by_ordering_mflups"] = orders
     forms = {}
-    for prec, k in (("f64x", 0), ("f32", 0), ("f32s", 0), ("f16s", 24), ("bf16s", 24)):
-        forms[prec] = timed(lat, prec, args.extra_steps, k)
+    for prec, k in (("f64", 0), ("f64x", 0), ("f32", 0), ("f32s", 0), ("f16s", 24),
+                    ("bf16s", 24)):
+        if prec != args.precision:
+            forms[prec] = timed(lat, prec, args.extra_steps, k)
     out["by_storage_mflups"] = forms
     return out
 
@@ -526,7 +552,7 @@ def main():
     ap.add_argument("--workload", default="large", choices=list(WORKLOADS))
     ap.add_argument("--ordering", default="blocked", choices=["lex", "blocked", "morton1",
                                                                "morton2"])
-    ap.add_argument("--precision", default="f64", choices=list(BYTES_PER_LUP))
+    ap.add_argument("--precision", default="f64x", choices=list(BYTES_PER_LUP))
     ap.add_argument("--extra-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extra", action="store_true")

@@ -32,6 +32,8 @@ namespace {
 
 struct FxCoef {
   int64_t hp, hm, w1p, a1;  // (1-w+)/2, (1-w-)/2, w+/18, w-/6, each * 2^63
+  int32_t hp_shift;         // when (1-w+)/2 = hp_sign * 2^-hp_shift exactly
+  int32_t hp_sign;
   int64_t q1;               // w+/36 (quadratic terms) * 2^63
   int64_t hF[3];            // F/2 in units U
   int64_t bF1[3];           // (1 - w-/2) F / 6 in units U
@@ -65,7 +67,9 @@ __device__ __forceinline__ int64_t fxmul(int64_t x, int64_t c63) { return __mul6
 #define LBM_FX_MIN_BLOCKS 3
 #endif
 
-template <bool REDUCE>
+// HP_POW2: (1 - w+)/2 is +-2^-k (w+ = 1.25, 1.5, 0.75, ...), so the nine
+// even-part products are shifts.
+template <bool REDUCE, bool HP_POW2>
 __global__ void __launch_bounds__(kSweepThreads, LBM_FX_MIN_BLOCKS)
     sweep_fx_kernel(const double* __restrict__ src, double* __restrict__ dst,
                     const int32_t* __restrict__ adj, int32_t n, FxCoef k, Coef<double> kd,
@@ -119,7 +123,10 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_FX_MIN_BLOCKS)
       int64_t out[19];
 #define LBM_FX_PAIR(P, QUAD, R, VX)                                         \
   {                                                                         \
-    const int64_t P_ = fxmul(S[P], k.hp) + R + (QUAD);                      \
+    const int64_t hS_ = HP_POW2 ? (k.hp_sign > 0 ? S[P] >> k.hp_shift       \
+                                                 : -(S[P] >> k.hp_shift))   \
+                                : fxmul(S[P], k.hp);                        \
+    const int64_t P_ = hS_ + R + (QUAD);                                    \
     const int64_t Q_ = fxmul(D[P], k.hm) + (VX);                            \
     out[2 * P + 1] = P_ + Q_;                                               \
     out[2 * P + 2] = P_ - Q_;                                               \
@@ -150,15 +157,20 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_FX_MIN_BLOCKS)
       const int64_t rem = drho - stored;
       d[0] = (rem + 8) >> 4;
       d[7] += rem - (d[0] << 4);
+      // Store the fixed-point result; an output that left its binary range
+      // (rare) is rewritten through FP64 in a separate branch, so the
+      // common path issues no FP64 instruction at all.
+      uint32_t out_of_range = 0;
 #pragma unroll
       for (int q = 0; q < 19; ++q) {
         const int64_t bits = wbits(q) + d[q];
-        double v;
-        if ((bits >> 52) == wexp(q))
-          v = __longlong_as_double(bits);
-        else
-          v = weight(q) + (double)(d[q] << wshift(q)) * 0x1p-58;
-        __stcs(dst + q * n + i, v);
+        out_of_range |= (uint32_t)((bits >> 52) != wexp(q)) << q;
+        __stcs(dst + q * n + i, __longlong_as_double(bits));
+      }
+      if (out_of_range) {
+        for (int q = 0; q < 19; ++q)
+          if ((out_of_range >> q) & 1u)
+            dst[q * n + i] = weight(q) + (double)(d[q] << wshift(q)) * 0x1p-58;
       }
       if (REDUCE) {
         red[0] = 1.0 + (double)drho * 0x1p-58;
@@ -195,6 +207,13 @@ int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const 
   const cudaStream_t stream = st->sp->stream;
   FxCoef k{};
   k.hp = c63(0.5 * (1.0 - wp));
+  // exact power of two (the mantissa of |hp| is 1/2) between 2^-1 and 2^-40
+  const double hp = 0.5 * (1.0 - wp);
+  int e = 0;
+  const double m = hp != 0.0 ? std::frexp(std::fabs(hp), &e) : 0.0;
+  const bool pow2 = m == 0.5 && -e + 1 >= 1 && -e + 1 <= 40;
+  k.hp_shift = pow2 ? 1 - e : 0;
+  k.hp_sign = hp < 0 ? -1 : 1;
   k.hm = c63(0.5 * (1.0 - wm));
   k.w1p = c63(wp / 18.0);
   k.a1 = c63(wm / 6.0);
@@ -210,9 +229,11 @@ int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const 
     double* dst = (double*)st->buf[st->cur ^ 1];
     if (n > 0) {
       if (t == n_steps - 1)
-        sweep_fx_kernel<true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials);
+        pow2 ? sweep_fx_kernel<true, true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials)
+             : sweep_fx_kernel<true, false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials);
       else
-        sweep_fx_kernel<false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials);
+        pow2 ? sweep_fx_kernel<false, true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials)
+             : sweep_fx_kernel<false, false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials);
     }
     st->cur ^= 1;
   }
