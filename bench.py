@@ -514,7 +514,7 @@ def run_ordering_study(args):
     flags = torch.from_numpy(bed.flags).cuda()
     rows = []
     orders = [("lex", (1, 1, 1))] + [("blocked", (b, b, b)) for b in (2, 4, 8, 16, 32, 64, 128)] + [
-        ("morton1", (1, 1, 1)), ("morton2", (1, 1, 1))]
+        ("morton1", (1, 1, 1)), ("morton2", (1, 1, 1)), ("hilbert", (1, 1, 1))]
     for name, block in orders:
         lat = SparseLattice(flags, name, block, bed.periodic)
         row = {"ordering": name if name != "blocked" else f"blocked {block[0]}"}
@@ -538,8 +538,21 @@ def run_ordering_study(args):
         del adj
         rows.append(row)
         lat.close()
+    # the tuner's pick from a 128-cell slab, and where it ranks at full size
+    from paper_1111_1129_gb300.autotune import tune_ordering
+    form = args.study_forms.split(",")[0] if "f64x" not in args.study_forms else "f64x"
+    best, table = tune_ordering(bed.flags, AXIS, bed.periodic, precision=form)
+    label = best[0] if best[0] != "blocked" else f"blocked {best[1][0]}"
+    full = sorted(((r[f"{form}_mflups"], r["ordering"]) for r in rows if f"{form}_mflups" in r),
+                  reverse=True)
+    rank = next((i + 1 for i, (_, o) in enumerate(full) if o == label), None)
+    tuned = {"form": form, "sample": "x in [0,128), periodic x", "pick": label,
+             "sample_table": [(n if n != "blocked" else f"blocked {b[0]}", v) for n, b, v in table],
+             "pick_full_size_rank": rank,
+             "pick_full_size_mflups": next((v for v, o in full if o == label), None),
+             "best_full_size": full[0] if full else None}
     print(json.dumps({"study": "ordering", "workload": WORKLOADS["large"][0],
-                      "steps_each": args.extra_steps, "rows": rows}), flush=True)
+                      "steps_each": args.extra_steps, "rows": rows, "tuner": tuned}), flush=True)
     return 0
 
 

@@ -75,6 +75,9 @@ extern "C" {
                                 3k+1 = y_k, 3k+2 = z_k */
 #define LBM_ORDER_MORTON2 3  /* Z curve, 2-bit groups: key bits 6k..6k+1 =
                                 x bits 2k..2k+1, then y, then z */
+#define LBM_ORDER_HILBERT 4  /* Hilbert curve over the enclosing 2^b cube
+                                (Skilling's transform); cells outside the
+                                box are skipped */
 
 typedef struct lbm_ordering {
   int32_t kind;      /* LBM_ORDER_* */

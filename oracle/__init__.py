@@ -30,7 +30,7 @@ _LIB = os.path.join(_HERE, "liblbm_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-ORDER_LEX, ORDER_BLOCKED, ORDER_MORTON1, ORDER_MORTON2 = 0, 1, 2, 3
+ORDER_LEX, ORDER_BLOCKED, ORDER_MORTON1, ORDER_MORTON2, ORDER_HILBERT = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:

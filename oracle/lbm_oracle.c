@@ -87,11 +87,54 @@ void oracle_velocity_set(int32_t* c /* [19][3] */, double* w /* [19] */, int32_t
  *         3k+2 = z_k.
  * kind 3: Z curve, 2-bit interleave: key bits 6k..6k+1 = x bits 2k..2k+1,
  *         6k+2..6k+3 = y bits 2k..2k+1, 6k+4..6k+5 = z bits 2k..2k+1.
+ * kind 4: Hilbert curve over the enclosing 2^b cube (b bits per axis, the
+ *         smallest b with 2^b >= every dimension), computed with Skilling's
+ *         transform ("Programming the Hilbert curve", AIP Conf. Proc. 707,
+ *         2004): coordinates -> "transposed" index by undoing the excess
+ *         rotations/reflections level by level and Gray-encoding, then the
+ *         index bits read level by level in the order x, y, z.
  */
+static int hilbert_bits(const int32_t dims[3]) {
+  int b = 1;
+  for (int k = 0; k < 3; ++k)
+    while ((1ll << b) < dims[k]) ++b;
+  return b;
+}
+
+static uint64_t hilbert_key(int bits, int64_t x, int64_t y, int64_t z) {
+  uint64_t X[3] = {(uint64_t)x, (uint64_t)y, (uint64_t)z};
+  const uint64_t top = 1ull << (bits - 1);
+  /* undo the excess work of the recursive construction, top level down */
+  for (uint64_t q = top; q > 1; q >>= 1) {
+    const uint64_t p = q - 1;
+    for (int i = 0; i < 3; ++i) {
+      if (X[i] & q) {
+        X[0] ^= p; /* invert the low bits of x */
+      } else {
+        const uint64_t t = (X[0] ^ X[i]) & p; /* exchange low bits of x and X[i] */
+        X[0] ^= t;
+        X[i] ^= t;
+      }
+    }
+  }
+  /* Gray encode */
+  for (int i = 1; i < 3; ++i) X[i] ^= X[i - 1];
+  uint64_t t = 0;
+  for (uint64_t q = top; q > 1; q >>= 1)
+    if (X[2] & q) t ^= q - 1;
+  for (int i = 0; i < 3; ++i) X[i] ^= t;
+  /* read the transposed index: level by level, x then y then z */
+  uint64_t key = 0;
+  for (int lvl = bits - 1; lvl >= 0; --lvl)
+    for (int i = 0; i < 3; ++i) key = (key << 1) | ((X[i] >> lvl) & 1ull);
+  return key;
+}
+
 uint64_t oracle_key(int32_t kind, const int32_t dims[3], const int32_t block[3], int64_t x,
                     int64_t y, int64_t z) {
   const int64_t nx = dims[0], ny = dims[1];
   if (kind == 0) return (uint64_t)(x + nx * (y + ny * z));
+  if (kind == 4) return hilbert_key(hilbert_bits(dims), x, y, z);
   if (kind == 1) {
     const int64_t bx = block[0], by = block[1], bz = block[2];
     const int64_t nbx = (dims[0] + bx - 1) / bx, nby = (dims[1] + by - 1) / by;

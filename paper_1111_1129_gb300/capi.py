@@ -16,6 +16,7 @@ from . import build as _build
 LBM_OK, LBM_EINVAL, LBM_EOVERFLOW, LBM_ECUDA = 0, -1, -2, -3
 LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ENOMEM, LBM_EFLAGS = -4, -5, -6, -7
 LBM_ORDER_LEX, LBM_ORDER_BLOCKED, LBM_ORDER_MORTON1, LBM_ORDER_MORTON2 = 0, 1, 2, 3
+LBM_ORDER_HILBERT = 4
 LBM_F64, LBM_F32, LBM_F32S, LBM_F16S, LBM_BF16S, LBM_F64X = 0, 1, 2, 3, 4, 5
 
 # Every exported entry point with (restype, argtypes); the symbol test checks

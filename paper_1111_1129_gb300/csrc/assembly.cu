@@ -163,7 +163,7 @@ int make_key_space(const int32_t dims[3], const lbm_ordering& ord, bool clamp_bl
   if (box >= (int64_t)1 << 31)
     return fail(LBM_EOVERFLOW, "box of %lld cells: the bounding box must stay below 2^31 cells",
                 (long long)box);
-  if (ord.kind < LBM_ORDER_LEX || ord.kind > LBM_ORDER_MORTON2)
+  if (ord.kind < LBM_ORDER_LEX || ord.kind > LBM_ORDER_HILBERT)
     return fail(LBM_EINVAL, "unknown ordering kind %d", ord.kind);
   if (ord.periodic > 7u) return fail(LBM_EINVAL, "periodic mask %u has bits beyond 0..2", ord.periodic);
   KeySpace s{};
@@ -193,12 +193,17 @@ int make_key_space(const int32_t dims[3], const lbm_ordering& ord, bool clamp_bl
   s.nbx = (s.nx + s.bx - 1) / s.bx;
   s.nby = (s.ny + s.by - 1) / s.by;
   s.nbz = (s.nz + s.bz - 1) / s.bz;
-  if (ord.kind == LBM_ORDER_BLOCKED)
+  s.hbits = 1;
+  while ((1LL << s.hbits) < s.nx || (1LL << s.hbits) < s.ny || (1LL << s.hbits) < s.nz) ++s.hbits;
+  if (ord.kind == LBM_ORDER_BLOCKED) {
     s.size = (uint64_t)(s.nbx * s.nby * s.nbz) * (uint64_t)(s.bx * s.by * s.bz);
-  else {
+  } else if (ord.kind == LBM_ORDER_HILBERT) {
+    // the Hilbert curve wanders through the whole enclosing cube
+    s.size = 1ull << (3 * s.hbits);
+  } else {
     s.size = ~0ull;
-    // every scheme here is monotone in each coordinate: the far corner holds
-    // the largest key
+    // lexicographic and Z-curve keys are monotone in each coordinate: the
+    // far corner holds the largest key
     s.size = key_of(s, s.nx - 1, s.ny - 1, s.nz - 1) + 1;
   }
   *ks = s;

@@ -57,11 +57,80 @@ struct KeySpace {
   int32_t kind;
   int64_t nx, ny, nz;
   int64_t bx, by, bz, nbx, nby, nbz;
+  int32_t hbits;  // Hilbert: bits per axis of the enclosing cube
   uint64_t size;  // every key is < size
 };
 
+// Hilbert curve on a 2^bits cube (Skilling, "Programming the Hilbert
+// curve", AIP Conf. Proc. 707, 2004): the coordinates become a "transposed"
+// index by undoing, from the top level down, the rotations and reflections
+// of the recursive construction and then Gray-encoding; the key reads the
+// transposed index level by level in the order x, y, z.
+__host__ __device__ inline uint64_t hilbert_encode(int bits, uint64_t x, uint64_t y, uint64_t z) {
+  uint64_t X[3] = {x, y, z};
+  const uint64_t top = 1ull << (bits - 1);
+  for (uint64_t q = top; q > 1; q >>= 1) {
+    const uint64_t p = q - 1;
+    for (int i = 0; i < 3; ++i) {
+      if (X[i] & q) {
+        X[0] ^= p;
+      } else {
+        const uint64_t t = (X[0] ^ X[i]) & p;
+        X[0] ^= t;
+        X[i] ^= t;
+      }
+    }
+  }
+  X[1] ^= X[0];
+  X[2] ^= X[1];
+  uint64_t t = 0;
+  for (uint64_t q = top; q > 1; q >>= 1)
+    if (X[2] & q) t ^= q - 1;
+  X[0] ^= t;
+  X[1] ^= t;
+  X[2] ^= t;
+  uint64_t key = 0;
+  for (int lvl = bits - 1; lvl >= 0; --lvl)
+    key = (key << 3) | (((X[0] >> lvl) & 1ull) << 2) | (((X[1] >> lvl) & 1ull) << 1) |
+          ((X[2] >> lvl) & 1ull);
+  return key;
+}
+
+// Inverse of hilbert_encode: Gray-decode the transposed index, then redo
+// the level transformations from the bottom up.
+__host__ __device__ inline void hilbert_decode(int bits, uint64_t key, uint64_t& x, uint64_t& y,
+                                               uint64_t& z) {
+  uint64_t X[3] = {0, 0, 0};
+  for (int lvl = 0; lvl < bits; ++lvl) {
+    X[0] |= ((key >> (3 * lvl + 2)) & 1ull) << lvl;
+    X[1] |= ((key >> (3 * lvl + 1)) & 1ull) << lvl;
+    X[2] |= ((key >> (3 * lvl)) & 1ull) << lvl;
+  }
+  const uint64_t t0 = X[2] >> 1;
+  X[2] ^= X[1];
+  X[1] ^= X[0];
+  X[0] ^= t0;
+  for (uint64_t q = 2; q != (1ull << bits); q <<= 1) {
+    const uint64_t p = q - 1;
+    for (int i = 2; i >= 0; --i) {
+      if (X[i] & q) {
+        X[0] ^= p;
+      } else {
+        const uint64_t t = (X[0] ^ X[i]) & p;
+        X[0] ^= t;
+        X[i] ^= t;
+      }
+    }
+  }
+  x = X[0];
+  y = X[1];
+  z = X[2];
+}
+
 __host__ __device__ inline uint64_t key_of(const KeySpace& ks, int64_t x, int64_t y, int64_t z) {
   switch (ks.kind) {
+    case LBM_ORDER_HILBERT:
+      return hilbert_encode(ks.hbits, (uint64_t)x, (uint64_t)y, (uint64_t)z);
     case LBM_ORDER_LEX:
       return (uint64_t)(x + ks.nx * (y + ks.ny * z));
     case LBM_ORDER_BLOCKED: {
@@ -114,6 +183,14 @@ __host__ __device__ inline bool cell_of(const KeySpace& ks, uint64_t k, int64_t&
       x = ix * ks.bx + lx;
       y = iy * ks.by + ly;
       z = iz * ks.bz + lz;
+      break;
+    }
+    case LBM_ORDER_HILBERT: {
+      uint64_t ux, uy, uz;
+      hilbert_decode(ks.hbits, k, ux, uy, uz);
+      x = (int64_t)ux;
+      y = (int64_t)uy;
+      z = (int64_t)uz;
       break;
     }
     case LBM_ORDER_MORTON1: {

@@ -14,7 +14,8 @@ import torch
 from . import capi
 
 ORDERINGS = {"lex": capi.LBM_ORDER_LEX, "blocked": capi.LBM_ORDER_BLOCKED,
-             "morton1": capi.LBM_ORDER_MORTON1, "morton2": capi.LBM_ORDER_MORTON2}
+             "morton1": capi.LBM_ORDER_MORTON1, "morton2": capi.LBM_ORDER_MORTON2,
+             "hilbert": capi.LBM_ORDER_HILBERT}
 PRECISIONS = {"f64": capi.LBM_F64, "f32": capi.LBM_F32, "f32s": capi.LBM_F32S,
               "f16s": capi.LBM_F16S, "bf16s": capi.LBM_BF16S, "f64x": capi.LBM_F64X}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f32s": 4, "f16s": 2, "bf16s": 2, "f64x": 8}
@@ -197,6 +198,32 @@ class LBMState:
     @property
     def steps(self) -> int:
         return capi.lbm_state_steps(self._handle)
+
+    def save(self, path: str, **meta) -> None:
+        """Checkpoint: the PDFs (decoded to FP64, which every storage form
+        round-trips exactly) with the lattice's identity, to ``path``
+        (.npz).  Extra keyword values are stored alongside."""
+        import numpy as np
+        lat = self.lattice
+        np.savez(path, pdfs=self.get_pdfs().cpu().numpy(), dims=np.array(lat.dims),
+                 ordering=np.array(lat.ordering), block=np.array(lat.block),
+                 periodic=np.array(lat.periodic), n=np.array(lat.n),
+                 cells=lat.cells().cpu().numpy(), precision=np.array(self.precision),
+                 scale_exp=np.array(self.scale_exp), steps=np.array(self.steps),
+                 **{k: np.asarray(v) for k, v in meta.items()})
+
+    def load(self, path: str) -> dict:
+        """Restore PDFs written by :meth:`save` into this state; the lattice
+        must be the same list (same cells in the same order).  Returns the
+        stored metadata."""
+        import numpy as np
+        with np.load(path) as z:
+            data = {k: z[k] for k in z.files}
+        if int(data["n"]) != self.n or not np.array_equal(data["cells"],
+                                                          self.lattice.cells().cpu().numpy()):
+            raise ValueError("checkpoint was written for a different cell list")
+        self.set_pdfs(torch.from_numpy(data["pdfs"]))
+        return data
 
     def synchronize(self, timeout_s: float = 0.0) -> None:
         capi.lbm_synchronize(self._handle, timeout_s)

@@ -14,7 +14,8 @@ ORDERS = [("lex", (1, 1, 1), oracle.ORDER_LEX),
           ("blocked", (2, 3, 5), oracle.ORDER_BLOCKED),
           ("blocked", (64, 64, 64), oracle.ORDER_BLOCKED),
           ("morton1", (1, 1, 1), oracle.ORDER_MORTON1),
-          ("morton2", (1, 1, 1), oracle.ORDER_MORTON2)]
+          ("morton2", (1, 1, 1), oracle.ORDER_MORTON2),
+          ("hilbert", (1, 1, 1), oracle.ORDER_HILBERT)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -92,3 +93,13 @@ def test_bad_flags_are_rejected():
     with pytest.raises(capi.LbmError) as ei:
         SparseLattice(torch.from_numpy(flags).cuda(), "lex")
     assert ei.value.status == capi.LBM_EFLAGS
+
+
+def test_ordering_tuner_on_a_sample():
+    from paper_1111_1129_gb300.autotune import DEFAULT_CANDIDATES, tune_ordering
+    bed = inputs.bed_medium(0)
+    best, table = tune_ordering(bed.flags, 0, bed.periodic, sample_length=32, steps=5)
+    assert len(table) == len(DEFAULT_CANDIDATES)
+    assert best == table[0][:2] and best in [(n, tuple(b)) for n, b in DEFAULT_CANDIDATES]
+    assert all(r[2] > 0 for r in table)
+    assert [r[2] for r in table] == sorted((r[2] for r in table), reverse=True)

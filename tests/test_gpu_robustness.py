@@ -1,0 +1,94 @@
+"""Checkpoint/resume and failure detection, with every failure made on the
+host side (no fault, trap or hang on the GPU): a wait that runs out of
+time returns LBM_ETIMEOUT and the context stays usable; a non-finite state
+is reported by the reduction; a resumed run continues bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1111_1129_gb300 import LBMState, SparseLattice, build, capi, inputs, omega_minus
+
+pytestmark = pytest.mark.gpu
+
+WP = 1.0 / 0.8
+WM = omega_minus(WP)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    capi.load()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f64x", "f32s", "f16s"])
+def test_checkpoint_resume_is_bit_exact(precision, tmp_path):
+    bed = inputs.bed_small(4)
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "morton1", periodic=bed.periodic)
+    F = (0.0, 0.0, 1e-5)
+    a = LBMState(lat, precision, 22)
+    a.step(30, WP, WM, F)
+    a.save(str(tmp_path / "ck.npz"), force=F)
+    a.step(25, WP, WM, F)
+    ref = a.get_pdfs()
+    ref_flux = a.reduce_flux(2)
+    b = LBMState(lat, precision, 22)
+    meta = b.load(str(tmp_path / "ck.npz"))
+    assert tuple(meta["force"]) == F and int(meta["steps"]) == 30
+    b.step(25, WP, WM, F)
+    assert torch.equal(b.get_pdfs(), ref)
+    assert b.reduce_flux(2) == ref_flux
+    other = SparseLattice(torch.from_numpy(bed.flags).cuda(), "lex", periodic=bed.periodic)
+    with pytest.raises(ValueError):
+        LBMState(other, precision, 22).load(str(tmp_path / "ck.npz"))
+    for h in (a, b, other, lat):
+        h.close()
+
+
+def test_wait_with_a_time_limit_reports_timeout_and_recovers():
+    bed = inputs.bed_medium(0)
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "blocked", (8, 8, 8), bed.periodic)
+    st = LBMState(lat, "f64")                  # IEEE FP64: ~0.5 ms per step here
+    st.step(2000, WP, WM, (1e-6, 0.0, 0.0))    # ~1 s of queued work
+    with pytest.raises(capi.LbmError) as ei:
+        st.synchronize(1e-3)
+    assert ei.value.status == capi.LBM_ETIMEOUT
+    st.synchronize(600.0)                      # the same work completes normally
+    capi.lbm_set_timeout(1e-3)
+    try:
+        st.step(2000, WP, WM, (1e-6, 0.0, 0.0))
+        with pytest.raises(capi.LbmError) as ei:
+            st.reduce_flux(0)
+        assert ei.value.status == capi.LBM_ETIMEOUT
+    finally:
+        capi.lbm_set_timeout(600.0)
+    mass, flux = st.reduce_flux(0)
+    assert abs(mass - lat.n) < 1e-9 * lat.n and flux > 0
+    st.close()
+    lat.close()
+
+
+def test_non_finite_state_is_reported():
+    bed = inputs.bed_small(0)
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "lex", periodic=bed.periodic)
+    st = LBMState(lat, "f64")
+    f = st.get_pdfs()
+    f[3, 17] = float("nan")
+    st.set_pdfs(f)
+    st.step(2, WP, WM, (0.0, 0.0, 1e-6))
+    with pytest.raises(capi.LbmError) as ei:
+        st.reduce_flux(2)
+    assert ei.value.status == capi.LBM_ENONFINITE
+    st.close()
+    lat.close()
+
+
+def test_errors_leave_a_readable_message_per_thread():
+    with pytest.raises(capi.LbmError):
+        capi.lbm_state_create(0, 0, 0)
+    assert "sparse" in capi.lbm_last_error()
+    import threading
+    seen = []
+    t = threading.Thread(target=lambda: seen.append(capi.lbm_last_error()))
+    t.start()
+    t.join()
+    assert seen == [""]

@@ -389,3 +389,37 @@ def test_adjoint_matches_finite_differences():
     h = 1e-6
     fd = (_J(flags, F, alpha, f0 + h * v, K) - _J(flags, F, alpha, f0 - h * v, K)) / (2 * h)
     assert abs(np.sum(lam0 * v) - fd) < 1e-7 * abs(fd)
+
+
+# ---------------------------------------------------------------------------
+# Hilbert curve (named among the numbering schemes in Sec. 3).
+
+@pytest.mark.parametrize("n", [2, 4, 8, 16])
+def test_hilbert_is_continuous_and_recursive(n):
+    """On a 2^k cube the Hilbert order starts at the origin, steps to a face
+    neighbour every time, and visits every aligned run of 8^j cells as one
+    2^j sub-cube (its recursive construction)."""
+    flags = np.zeros((n, n, n), np.uint8)
+    cells, _, _ = oracle.build_sparse(flags, oracle.ORDER_HILBERT)
+    xyz = np.stack([cells % n, (cells // n) % n, cells // (n * n)], axis=1)
+    assert tuple(xyz[0]) == (0, 0, 0)
+    assert np.all(np.abs(np.diff(xyz, axis=0)).sum(axis=1) == 1)
+    j = 1
+    while 2 ** j <= n:
+        run = 8 ** j
+        for b in range(0, n ** 3, run):
+            block = xyz[b:b + run]
+            assert np.all(block.max(axis=0) - block.min(axis=0) == 2 ** j - 1)
+            assert np.all(block.min(axis=0) % 2 ** j == 0)
+        j += 1
+
+
+def test_hilbert_non_power_of_two_is_the_cube_order_restricted():
+    dims = (6, 3, 5)
+    flags = np.zeros(dims[::-1], np.uint8)
+    cells, _, _ = oracle.build_sparse(flags, oracle.ORDER_HILBERT)
+    cube = np.zeros((8, 8, 8), np.uint8)
+    cc, _, _ = oracle.build_sparse(cube, oracle.ORDER_HILBERT)
+    ref = [(int(c % 8), int((c // 8) % 8), int(c // 64)) for c in cc]
+    ref = [p for p in ref if p[0] < 6 and p[1] < 3 and p[2] < 5]
+    assert _order_cells(cells, dims) == ref
