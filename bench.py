@@ -411,6 +411,60 @@ def run_precision_study(args):
     return 0
 
 
+def run_adjoint_study(args):
+    """The 128^3 bed with per-cell Brinkman damping (uniform in [0, 0.05)),
+    FP32 shifted storage, K = 2000 steps, checkpoints every 45 steps: time
+    of a plain forward run, of the checkpointed forward pass and of the
+    reverse pass, and the memory the adjoint holds."""
+    import torch
+
+    from paper_1111_1129_gb300 import Adjoint, LBMState, SparseLattice, capi, inputs, omega_minus
+
+    capi.load()
+    wm = omega_minus(WP)
+    bed = inputs.bed_cube128(0)
+    alpha_dense = inputs.alpha_field(bed.dims, seed=0)
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "blocked", (8, 8, 8), bed.periodic)
+    alpha = torch.from_numpy(alpha_dense.reshape(-1)[lat.cells().cpu().numpy()].copy()).cuda()
+    K, stride, F = args.adjoint_steps, 45, (0.0, 0.0, 1e-6)
+    out = {}
+    for prec in ("f32s", "f64"):
+        st = LBMState(lat, prec)
+        st.set_damping(alpha)
+
+        def timed(fn):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            return r, time.perf_counter() - t0
+
+        st.step(3, WP, wm, F)
+        st.reset()
+        _, t_fwd = timed(lambda: (st.step(K, WP, wm, F), st.reduce_flux(2)))
+        st.reset()
+        torch.cuda.reset_peak_memory_stats()
+        free0 = torch.cuda.mem_get_info()[0]
+        adj = Adjoint(st, K, stride)
+        held = free0 - torch.cuda.mem_get_info()[0]
+        J, t_af = timed(lambda: adj.forward(WP, wm, F, 2))
+        (dF, da, _), t_ab = timed(lambda: adj.backward())
+        state_bytes = lat.n * 19 * (4 if prec == "f32s" else 8)
+        out[prec] = {"forward_s": t_fwd, "adjoint_forward_s": t_af, "adjoint_backward_s": t_ab,
+                     "adjoint_total_over_forward": (t_af + t_ab) / t_fwd,
+                     "adjoint_device_bytes": held,
+                     "adjoint_bytes_over_one_state": held / state_bytes,
+                     "J": J, "dJdFz": dF[2]}
+        adj.close()
+        st.close()
+    line = {"study": "adjoint", "workload": "packed bed 128^3, tube D=126 along z, spheres r=6, "
+            "damping U[0,0.05)", "fluid_cells": lat.n, "steps": K, "checkpoint_stride": stride,
+            "forms": out}
+    lat.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batch_study(args):
     """256 packed beds (cube sides uniform in {24..96}, sphere radii in
     [3, 8], forces in [1e-7, 1e-5] along z), FP32 shifted storage: the
@@ -579,7 +633,12 @@ def main():
     ap.add_argument("--ordering-study", action="store_true",
                     help="run the numbering-scheme study instead of the benchmark")
     ap.add_argument("--study-forms", default="f64,f32s,f16s")
+    ap.add_argument("--adjoint-study", action="store_true",
+                    help="time the checkpointed adjoint against the forward run")
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
     args = ap.parse_args()
+    if args.adjoint_study:
+        return run_adjoint_study(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.precision_study:

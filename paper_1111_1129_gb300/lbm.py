@@ -199,6 +199,10 @@ class LBMState:
     def steps(self) -> int:
         return capi.lbm_state_steps(self._handle)
 
+    def reset(self) -> None:
+        """Back to rest (f_q = w_q); clears the step count."""
+        capi.lbm_state_reset(self._handle)
+
     def save(self, path: str, **meta) -> None:
         """Checkpoint: the PDFs (decoded to FP64, which every storage form
         round-trips exactly) with the lattice's identity, to ``path``
