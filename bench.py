@@ -43,11 +43,16 @@ BYTES_PER_LUP = {"f64": 19 * 8 * 2 + 18 * 4, "f64x": 19 * 8 * 2 + 18 * 4,
                  "f32": 19 * 4 * 2 + 18 * 4,
                  "f32s": 19 * 4 * 2 + 18 * 4, "f16s": 19 * 2 * 2 + 18 * 4,
                  "bf16s": 19 * 2 * 2 + 18 * 4}
-# DRAM bytes (read + write) per fluid update measured by ncu on the
-# 256x128x128 bed (profiles/sweep_*_bed256x128x128_ncu.md); the roofline's
-# `traffic` scales them to the benchmark's cells.  Reset an entry to None
-# when its kernel changes.
-MEASURED_DRAM_BYTES_PER_LUP = {"f64x": 351.2, "f64": 347.8}
+# DRAM bytes (read + write) per fluid update of one sweep launch, measured by
+# ncu per (workload, form): the full-size bed in one 1-pass capture
+# (profiles/sweep_f64x_f32s_f16s_bed1024x256x256_dram.md), the 256x128x128
+# bed in the --set full captures (profiles/sweep_*_bed256x128x128_ncu.md).
+# The roofline's `traffic` multiplies them by the benchmark's cells.  Drop an
+# entry when its kernel changes.
+MEASURED_DRAM_BYTES_PER_LUP = {
+    ("large", "f64x"): 383.0, ("large", "f32s"): 231.0, ("large", "f16s"): 152.3,
+    ("medium", "f64x"): 351.2, ("medium", "f64"): 347.8,
+}
 STORAGE = {"f64": "f64", "f64x": "f64", "f32": "f32", "f32s": "f32 (f - w)",
            "f16s": "f16 ((f - w) 2^k)", "bf16s": "bf16 ((f - w) 2^k)"}
 ARITHMETIC = {"f64": "f64", "f64x": "int64", "f32": "f32", "f32s": "f32", "f16s": "f32",
@@ -298,8 +303,9 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": (MEASURED_DRAM_BYTES_PER_LUP[args.precision] * n
-                                 if MEASURED_DRAM_BYTES_PER_LUP.get(args.precision) else None),
+                     "traffic": (MEASURED_DRAM_BYTES_PER_LUP[key] * n
+                                 if (key := (args.workload, args.precision))
+                                 in MEASURED_DRAM_BYTES_PER_LUP else None),
                      "bytes_per_lup": bpl, "peak_kind": peak_kind,
                      "kernel": "sweep_fx_kernel" if args.precision == "f64x"
                      else f"sweep_kernel<{args.precision}>"},
@@ -618,7 +624,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=list(WORKLOADS))
     ap.add_argument("--ordering", default="blocked", choices=["lex", "blocked", "morton1",
-                                                               "morton2"])
+                                                               "morton2", "hilbert"])
     ap.add_argument("--precision", default="f64x", choices=list(BYTES_PER_LUP))
     ap.add_argument("--extra-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -225,8 +225,21 @@ __device__ __forceinline__ void gather(const typename Form<PREC>::S* __restrict_
   for (int q = 1; q < 19; ++q) g[q] = decode<PREC>(load_ro<PREC>(src + idx[q - 1]), inv_scale);
 }
 
+#ifndef LBM_SWEEP_MIN_BLOCKS
+#define LBM_SWEEP_MIN_BLOCKS 1
+#endif
+// Resident 256-thread blocks per SM that the register budget of the FP32 and
+// 16-bit sweeps is sized for (the FP64 sweep is bound by its arithmetic).
+// With 1 the compiler keeps all 18 indices and 19 pulled values of a cell in
+// flight (64 registers, 4 blocks per SM); on the 1024x256x256 bed forcing 5,
+// 6, 7 or 8 blocks per SM cut the FP16 sweep by 3%, 4%, 8% and 8%.
+template <int PREC>
+constexpr int sweep_min_blocks() {
+  return PREC == LBM_F64 ? 1 : LBM_SWEEP_MIN_BLOCKS;
+}
+
 template <int PREC, bool DAMPED, bool REDUCE>
-__global__ void __launch_bounds__(kSweepThreads)
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<PREC>())
     sweep_kernel(const typename Form<PREC>::S* __restrict__ src,
                  typename Form<PREC>::S* __restrict__ dst, const int32_t* __restrict__ adj,
                  int32_t n, Coef<typename Form<PREC>::C> k,
