@@ -169,15 +169,15 @@ __global__ void __launch_bounds__(kSweepThreads)
   if (i < n) {
     int32_t idx[18];
 #pragma unroll
-    for (int q = 0; q < 18; ++q) idx[q] = __ldg(adj + q * n + i);
+    for (int q = 0; q < 18; ++q) idx[q] = __ldcs(adj + q * n + i);
+    // all 36 pulls of the cell are independent: issue them back to back
     C lf[19], g[19];
     lf[0] = lam_in[i];
     g[0] = decode<PREC>(load_ro<PREC>(f_prev + i), k.inv_scale);
 #pragma unroll
-    for (int q = 1; q < 19; ++q) {
-      lf[q] = lam_in[reverse_slot(q, idx[opp(q) - 1], n, i)];
-      g[q] = decode<PREC>(load_ro<PREC>(f_prev + idx[q - 1]), k.inv_scale);
-    }
+    for (int q = 1; q < 19; ++q) g[q] = decode<PREC>(load_ro<PREC>(f_prev + idx[q - 1]), k.inv_scale);
+#pragma unroll
+    for (int q = 1; q < 19; ++q) lf[q] = __ldg(lam_in + reverse_slot(q, idx[opp(q) - 1], n, i));
     C u[3], s;
     const C al = DAMPED ? alpha[i] : C(0);
     velocity<C, DAMPED>(g, k, al, u, s);
