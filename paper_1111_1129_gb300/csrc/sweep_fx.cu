@@ -14,14 +14,15 @@
 //  * Pair sums/differences, rho - 1 and j are then exact integer sums.
 //  * Products with the relaxation constants use 64x64 -> high-64 integer
 //    multiplies with the constants scaled by 2^63 (relative precision
-//    2^-62).  The quadratic velocity terms, ~u^2 ~ 1e-10 of f, are done in
-//    FP32 (absolute error ~1e-17) and rounded to units.
+//    2^-62).  The quadratic velocity terms come from the six products
+//    u_a u_b, each built from three 32x32 -> 64 integer products and exact
+//    to 2 units (7e-18); this needs |u| < 2^-6.
 //  * After rounding to the storage units, the rest population takes the
 //    remainder rho - 1 - sum_{q>0} X*_q (and a diagonal population the last
 //    sub-unit part), so every collision conserves the stored mass exactly.
 //
-// A cell with any PDF outside its range (fast flow, random test states,
-// NaN) takes the IEEE FP64 collision instead, and an output that leaves its
+// A cell with any PDF outside its range or with |u| >= 2^-6 (fast flow,
+// random test states, NaN) takes the IEEE FP64 collision instead, and an output that leaves its
 // range is written through FP64; both are exact to FP64 round-off.  The
 // update is the TRT update of the FP64 form (same pair formulation), with
 // errors below FP64 round-off of f.
@@ -61,21 +62,62 @@ __device__ __forceinline__ int wshift(int q) { return q == 0 ? 4 : (q <= 6 ? 1 :
 __device__ __forceinline__ int64_t fxmul(int64_t x, int64_t c63) { return __mul64hi(2 * x, c63); }
 
 // Resident blocks of 256 threads per SM the register budget is fitted to:
-// 3 (80 registers) measured 13.2 GLUP/s on the 1024x256x256 bed against
-// 11.5 for 2 (120 registers) and 12.6 for 4 (64 registers, heavy spills).
+// on the 1024x256x256 bed 3 (80 registers) beat 2 (120 registers) by 15%
+// and 4 (64 registers, heavy spills) by 5%.  The reducing variant, which
+// runs once per lbm_step call and also carries the block sums, is fitted
+// to 2: without spills it takes 2.46 ms per launch there against 2.69 ms.
 #ifndef LBM_FX_MIN_BLOCKS
 #define LBM_FX_MIN_BLOCKS 3
 #endif
 
+// Block sums of rho and u for the flux reduction.  A cell on the fixed-point
+// path gives exact int64 moments in units U (rho - 1 below 2^57.4 and u
+// below 2^56 in magnitude, so a warp's sum stays below 2^63); they are summed
+// exactly per warp and converted to FP64 once per warp.  A cell that took
+// the IEEE path gives FP64 rho and u, summed only in warps that have one.
+// The per-warp values are then added in warp order: the result is
+// deterministic and rounds once per warp instead of once per cell.
+__device__ __forceinline__ void fx_block_sum(int64_t iv[4], int nfix, double dv[4], bool ieee,
+                                             double* out) {
+  __shared__ double sm[kSweepThreads / 32][4];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) iv[j] += __shfl_down_sync(0xffffffffu, iv[j], o);
+    nfix += __shfl_down_sync(0xffffffffu, nfix, o);
+  }
+  if (__any_sync(0xffffffffu, ieee)) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) dv[j] += __shfl_down_sync(0xffffffffu, dv[j], o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    sm[warp][0] = ((double)nfix + (double)iv[0] * 0x1p-58) + dv[0];
+#pragma unroll
+    for (int j = 1; j < 4; ++j) sm[warp][j] = (double)iv[j] * 0x1p-58 + dv[j];
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double acc = 0.0;
+#pragma unroll
+    for (int w = 0; w < kSweepThreads / 32; ++w) acc += sm[w][threadIdx.x];
+    out[threadIdx.x] = acc;
+  }
+}
+
 // HP_POW2: (1 - w+)/2 is +-2^-k (w+ = 1.25, 1.5, 0.75, ...), so the nine
 // even-part products are shifts.
 template <bool REDUCE, bool HP_POW2>
-__global__ void __launch_bounds__(kSweepThreads, LBM_FX_MIN_BLOCKS)
+__global__ void __launch_bounds__(kSweepThreads, REDUCE ? 2 : LBM_FX_MIN_BLOCKS)
     sweep_fx_kernel(const double* __restrict__ src, double* __restrict__ dst,
                     const int32_t* __restrict__ adj, int32_t n, FxCoef k, Coef<double> kd,
                     double* __restrict__ partials) {
   const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
-  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  double red[4] = {0.0, 0.0, 0.0, 0.0};   // IEEE-path cells: rho, u
+  int64_t ired[4] = {0, 0, 0, 0};         // fixed-point cells: rho - 1, u in units U
+  int nfix = 0;
   if (i < n) {
     int32_t idx[18];
 #pragma unroll
@@ -173,10 +215,11 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_FX_MIN_BLOCKS)
             dst[q * n + i] = weight(q) + (double)(d[q] << wshift(q)) * 0x1p-58;
       }
       if (REDUCE) {
-        red[0] = 1.0 + (double)drho * 0x1p-58;
-        red[1] = (double)ux * 0x1p-58;
-        red[2] = (double)uy * 0x1p-58;
-        red[3] = (double)uz * 0x1p-58;
+        ired[0] = drho;
+        ired[1] = ux;
+        ired[2] = uy;
+        ired[3] = uz;
+        nfix = 1;
       }
     } else {
       double g[19];
@@ -194,7 +237,7 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_FX_MIN_BLOCKS)
       }
     }
   }
-  if (REDUCE) block_sum4(red, partials + 4 * (int64_t)blockIdx.x);
+  if (REDUCE) fx_block_sum(ired, nfix, red, i < n && nfix == 0, partials + 4 * (int64_t)blockIdx.x);
 }
 
 int64_t c63(double c) { return (int64_t)std::llround(c * 0x1p63); }
