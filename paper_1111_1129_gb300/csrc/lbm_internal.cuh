@@ -256,6 +256,18 @@ struct Batch {
   double g_wp, g_wm;
   int use_graph;
 };
+
+// Single-state step graphs: kGraphSteps non-reducing steps captured once per
+// grid parity and replayed by long lbm_step calls.  kGraphSteps is even, so
+// a replay leaves the parity where it found it.  A graph is keyed by the
+// launch arguments it baked in.
+constexpr int32_t kGraphSteps = 128;
+struct StepGraph {
+  cudaStream_t capture;     // private stream the launches are captured on
+  cudaGraphExec_t exec[2];  // per parity of st->cur, or null
+  double wp[2], wm[2], F[2][3];
+  const void* alpha[2];
+};
 }  // namespace lbm
 
 struct lbm_state {
@@ -274,6 +286,7 @@ struct lbm_state {
   double last_force[3];
   double last_wp, last_wm;
   cudaEvent_t done;    // recorded to wait for the stream with a time limit
+  lbm::StepGraph* graph;  // cached CUDA graphs of non-reducing steps, or null
   lbm::Batch* batch;   // non-null for a batched state (sp is then owned)
 };
 
@@ -284,8 +297,10 @@ void free_adjoint(lbm_adjoint* ad);
 size_t storage_bytes(int prec);   // bytes per stored PDF of a precision form
 size_t compute_bytes(int prec);   // bytes of the arithmetic type of a form
 bool is_shifted(int prec);        // stores f - w_q rather than f
-// Fixed-point FP64-storage sweep (sweep_fx.cu), undamped.
-int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3]);
+// Fixed-point FP64-storage sweep (sweep_fx.cu), undamped: n_steps launches
+// on `stream`; the last one writes the block sums when reduce_last is set.
+int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3],
+                    cudaStream_t stream, bool reduce_last);
 bool valid_state(const lbm_state* st);
 // Records `ev` on `stream` and polls it with a wall-clock limit (<= 0: the
 // library default); LBM_ETIMEOUT if the work is still running then.

@@ -102,13 +102,13 @@ bool valid_state(const lbm_state* st) { return st && st->magic == kMagicState; }
 namespace {
 
 template <int PREC>
-int launch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3]) {
+int launch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3],
+                 cudaStream_t stream, bool reduce_last) {
   using S = typename Form<PREC>::S;
   using C = typename Form<PREC>::C;
   const int32_t n = (int32_t)st->sp->n;
-  const cudaStream_t stream = st->sp->stream;
   if constexpr (PREC == LBM_F64X) {
-    if (!st->alpha) return launch_steps_fx(st, n_steps, wp, wm, F);
+    if (!st->alpha) return launch_steps_fx(st, n_steps, wp, wm, F, stream, reduce_last);
   }
   const Coef<C> k = make_coef<C>(wp, wm, F, st->scale_exp);
   const unsigned grid = (unsigned)st->nblocks;
@@ -116,7 +116,7 @@ int launch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const dou
   for (int32_t t = 0; t < n_steps; ++t) {
     const S* src = (const S*)st->buf[st->cur];
     S* dst = (S*)st->buf[st->cur ^ 1];
-    const bool last = t == n_steps - 1;
+    const bool last = reduce_last && t == n_steps - 1;
     if (n > 0) {
       if (alpha) {
         if (last) sweep_kernel<PREC, true, true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, st->partials);
@@ -185,8 +185,90 @@ int dispatch_set(lbm_state* st, const double* f, int from_rest) {
   LBM_DISPATCH(st->precision, launch_set, st, f, from_rest)
 }
 int dispatch_get(const lbm_state* st, double* f) { LBM_DISPATCH(st->precision, launch_get, st, f) }
-int dispatch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3]) {
-  LBM_DISPATCH(st->precision, launch_steps, st, n_steps, wp, wm, F)
+int dispatch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3],
+                   cudaStream_t stream, bool reduce_last) {
+  LBM_DISPATCH(st->precision, launch_steps, st, n_steps, wp, wm, F, stream, reduce_last)
+}
+
+void free_graph(lbm_state* st) {
+  StepGraph* g = st->graph;
+  if (!g) return;
+  for (int p = 0; p < 2; ++p)
+    if (g->exec[p]) cudaGraphExecDestroy(g->exec[p]);
+  if (g->capture) cudaStreamDestroy(g->capture);
+  delete g;
+  st->graph = nullptr;
+}
+
+// The graph of kGraphSteps non-reducing steps from the current parity with
+// these arguments, captured on first use (or when the arguments changed).
+int step_graph(lbm_state* st, double wp, double wm, const double F[3], cudaGraphExec_t* out) {
+  if (!st->graph) {
+    st->graph = new StepGraph{};
+    const cudaError_t e = cudaStreamCreateWithFlags(&st->graph->capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      free_graph(st);
+      return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+  }
+  StepGraph* g = st->graph;
+  const int p = st->cur;
+  if (g->exec[p] && g->wp[p] == wp && g->wm[p] == wm && g->F[p][0] == F[0] &&
+      g->F[p][1] == F[1] && g->F[p][2] == F[2] && g->alpha[p] == st->alpha) {
+    *out = g->exec[p];
+    return LBM_OK;
+  }
+  if (g->exec[p]) {
+    cudaGraphExecDestroy(g->exec[p]);
+    g->exec[p] = nullptr;
+  }
+  LBM_CUDA_TRY(cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal));
+  const int rc = dispatch_steps(st, kGraphSteps, wp, wm, F, g->capture, false);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(g->capture, &graph);
+  st->cur = p;   // the capture only recorded the launches
+  if (rc != LBM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  const cudaError_t e2 = cudaGraphInstantiate(&g->exec[p], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) {
+    g->exec[p] = nullptr;
+    return cuda_fail(e2, "cudaGraphInstantiate");
+  }
+  g->wp[p] = wp;
+  g->wm[p] = wm;
+  for (int d = 0; d < 3; ++d) g->F[p][d] = F[d];
+  g->alpha[p] = st->alpha;
+  *out = g->exec[p];
+  return LBM_OK;
+}
+
+// n_steps steps on the state's stream.  Launching a kernel costs the host a
+// few microseconds, as much as a whole step of a bed of ~10^5 cells, so a
+// call long enough to replay the cached graph of kGraphSteps steps at least
+// twice runs its bulk that way; the remaining steps, the reducing last one
+// included, are launched one by one.  The kernels and their order are the
+// same either way, so the results are bit-identical.
+int run_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3]) {
+  const cudaStream_t stream = st->sp->stream;
+  int32_t replays = st->sp->n > 0 ? (n_steps - 1) / kGraphSteps : 0;
+  if (replays >= 2) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    LBM_CUDA_TRY(cudaStreamIsCapturing(stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone) replays = 0;   // the caller is capturing
+  } else {
+    replays = 0;
+  }
+  if (replays > 0) {
+    cudaGraphExec_t exec = nullptr;
+    const int rc = step_graph(st, wp, wm, F, &exec);
+    if (rc != LBM_OK) return rc;
+    for (int32_t r = 0; r < replays; ++r) LBM_CUDA_TRY(cudaGraphLaunch(exec, stream));
+  }
+  return dispatch_steps(st, n_steps - replays * kGraphSteps, wp, wm, F, stream, true);
 }
 int dispatch_moments(const lbm_state* st, double* rho, double* u) {
   LBM_DISPATCH(st->precision, launch_moments, st, rho, u)
@@ -202,6 +284,7 @@ void free_state(lbm_state* st) {
     if (p) cudaFree(p);
   if (st->red_host) cudaFreeHost(st->red_host);
   if (st->done) cudaEventDestroy(st->done);
+  free_graph(st);
   if (st->batch) free_batch(st);
   st->magic = 0;
   delete st;
@@ -321,7 +404,7 @@ extern "C" int lbm_step(lbm_state* st, int32_t n_steps, double omega_plus, doubl
     if (!std::isfinite(force[d])) return fail(LBM_EINVAL, "force[%d] is not finite", d);
   if (n_steps == 0) return LBM_OK;
   const int rc = st->batch ? batch_steps(st, n_steps, omega_plus, omega_minus, force)
-                           : dispatch_steps(st, n_steps, omega_plus, omega_minus, force);
+                           : run_steps(st, n_steps, omega_plus, omega_minus, force);
   if (rc != LBM_OK) return rc;
   st->steps += n_steps;
   st->last_wp = omega_plus;

@@ -245,9 +245,9 @@ int64_t units(double v) { return (int64_t)std::llround(v * 0x1p58); }
 
 }  // namespace
 
-int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3]) {
+int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3],
+                    cudaStream_t stream, bool reduce_last) {
   const int32_t n = (int32_t)st->sp->n;
-  const cudaStream_t stream = st->sp->stream;
   FxCoef k{};
   k.hp = c63(0.5 * (1.0 - wp));
   // exact power of two (the mantissa of |hp| is 1/2) between 2^-1 and 2^-40
@@ -271,7 +271,7 @@ int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const 
     const double* src = (const double*)st->buf[st->cur];
     double* dst = (double*)st->buf[st->cur ^ 1];
     if (n > 0) {
-      if (t == n_steps - 1)
+      if (reduce_last && t == n_steps - 1)
         pow2 ? sweep_fx_kernel<true, true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials)
              : sweep_fx_kernel<true, false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials);
       else
