@@ -174,7 +174,12 @@ int lbm_set_damping(lbm_state* st, const double* alpha_dev);
  * even / odd relaxation rates, each in (0, 2); force is a host double[3]
  * body force, finite.  The last step of the call also writes FP64 block
  * partial sums of rho and u for lbm_reduce_flux.  Asynchronous on the
- * state's stream.  Errors: LBM_EINVAL, LBM_ECUDA.
+ * state's stream.  A call of more than 256 steps replays a CUDA graph of
+ * 128 steps, which the state captures on a private stream the first time
+ * (per grid parity and per set of rates, force and damping pointer) and
+ * keeps until lbm_free; the kernels and results are those of launching
+ * every step, and a stream that is itself being captured gets plain
+ * launches.  Errors: LBM_EINVAL, LBM_ECUDA.
  */
 int lbm_step(lbm_state* st, int32_t n_steps, double omega_plus, double omega_minus,
              const double force[3]);
