@@ -1,0 +1,69 @@
+"""The index-range limits of the int32 adjacency, at full size.
+
+A flow slot is addressed as q*N + m in int32, so the library accepts at most
+19*N < 2^31 fluid cells (N <= 113,025,455).  An all-fluid periodic box just
+below that limit (1024 x 512 x 215 = 112,721,920 cells, the last PDF slot
+at 2,141,716,479) is assembled and stepped in the FP64-storage form: every
+cell sees the same history, so every cell's moments must equal those of a
+single periodic cell stepped by the oracle, and the mass must stay N.  Any
+index that wrapped past 2^31 would break that uniformity.  A slightly
+larger all-fluid box (1024 x 512 x 256, 19*N = 2.55e9) must be refused with
+LBM_EOVERFLOW before any PDF or adjacency memory is taken.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1111_1129_gb300 import LBMState, SparseLattice, build, capi, omega_minus
+
+pytestmark = pytest.mark.gpu
+
+WP = 1.0 / 0.8
+WM = omega_minus(WP)
+F = (3e-6, -1e-6, 2e-6)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def library():
+    build.build()
+    capi.load()
+
+
+def test_largest_list_steps_uniformly():
+    dims = (1024, 512, 215)          # x, y, z
+    n_box = dims[0] * dims[1] * dims[2]
+    assert 19 * n_box < 2 ** 31 <= 19 * 1024 * 512 * 216
+    flags = torch.zeros((dims[2], dims[1], dims[0]), dtype=torch.uint8, device="cuda")
+    lat = SparseLattice(flags, "lex", periodic=0b111)
+    del flags
+    assert lat.n == n_box
+    st = LBMState(lat, "f64x")
+    st.step(2, WP, WM, F)
+    mass, flux = st.reduce_flux(0)
+    rho, u = st.moments()
+    # one periodic cell, two steps, in the oracle
+    one = np.zeros((1, 1, 1), np.uint8)
+    _, obs, rho1, u1 = oracle.run(one, 0b111, WP, WM, F, 2)
+    # u ~ 1e-6 is a sum of +-f ~ 0.03: FP64 round-off of the sums is ~1e-17
+    # absolute, ~1e-11 relative, and the two sides sum in different orders
+    assert mass == float(n_box)                     # rest + force: rho = 1 exactly
+    assert abs(flux - u1[0, 0, 0, 0]) <= 1e-10 * abs(u1[0, 0, 0, 0])
+    for d in range(3):
+        col = u[d]
+        assert torch.equal(col, col[:1].expand_as(col)), d   # every cell identical
+        assert abs(float(col[0]) - u1[d, 0, 0, 0]) <= 1e-10 * abs(u1[d, 0, 0, 0])
+    assert torch.equal(rho, rho[:1].expand_as(rho))
+    assert abs(float(rho[0]) - rho1[0, 0, 0]) <= 1e-15
+    del rho, u
+    st.close()
+    lat.close()
+
+
+def test_list_beyond_the_slot_range_is_refused():
+    dims = (1024, 512, 256)
+    flags = torch.zeros((dims[2], dims[1], dims[0]), dtype=torch.uint8, device="cuda")
+    with pytest.raises(capi.LbmError) as ei:
+        SparseLattice(flags, "lex", periodic=0b111)
+    assert ei.value.status == capi.LBM_EOVERFLOW
+    assert "19*N" in str(ei.value)
