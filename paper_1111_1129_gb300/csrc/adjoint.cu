@@ -278,9 +278,9 @@ struct Runner {
 
   void step(const S* src, S* dst) const {
     if (alpha)
-      sweep_kernel<PREC, true, false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, nullptr);
+      sweep_kernel<PREC, true, kNoReduce><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, nullptr);
     else
-      sweep_kernel<PREC, false, false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, nullptr);
+      sweep_kernel<PREC, false, kNoReduce><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, nullptr);
   }
   void seed(const S* f_prev) const {
     if (alpha)
@@ -386,7 +386,7 @@ int finish_sums(lbm_adjoint* ad) {
     for (int j = 0; j < 4; ++j) ad->red_host[j] = 0.0;
     return LBM_OK;
   }
-  final_sum_kernel<<<1, 1024, 0, stream>>>(ad->part, ad->st->nblocks, ad->red_dev);
+  final_sum_kernel<<<1, 1024, 0, stream>>>(ad->part, ad->st->nblocks, 1, ad->red_dev);
   LBM_CUDA_TRY(cudaGetLastError());
   LBM_CUDA_TRY(cudaMemcpyAsync(ad->red_host, ad->red_dev, 4 * sizeof(double),
                                cudaMemcpyDeviceToHost, stream));

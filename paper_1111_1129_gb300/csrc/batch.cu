@@ -68,42 +68,45 @@ __global__ void __launch_bounds__(512)
     kb.hF[d] = bf.hF[d];
     kb.bF1[d] = bf.bF1[d];
   }
-  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  C rho = C(0), u[3] = {C(0), C(0), C(0)};
+  bool live = false;
 #pragma unroll
   for (int j = 0; j < CPT; ++j) {
     const int64_t i = base + (int64_t)j * blockDim.x + threadIdx.x;
     if (i < end) {
       C g[19];
       gather<PREC>(src, adj, n, (int32_t)i, kb.inv_scale, g);
-      C rho, u[3];
       collide<C, false>(g, kb, C(0), rho, u);
+      live = true;
 #pragma unroll
       for (int q = 0; q < 19; ++q)
         store_stream<PREC>(dst + q * n + i, encode<PREC>(g[q], kb.scale));
-      if (REDUCE) {
-        red[0] = (double)rho;
-        red[1] = (double)u[0];
-        red[2] = (double)u[1];
-        red[3] = (double)u[2];
-      }
     }
   }
-  if (REDUCE) block_sum4(red, partials + 4 * (int64_t)blockIdx.x);
+  if constexpr (REDUCE) {   // runs with 256 threads and CPT = 1
+    double w[4];
+    warp_flux_sums<C, Form<PREC>::kShifted>(live, rho, u, w);
+    store_warp_sums(w, partials);
+  }
 }
 
-// Per-bed final sums over the bed's 256-cell block partials, in the same
-// order as the single-bed final sum.
+// Per-bed final sums over the warp sums of the bed's 256-cell blocks, in the
+// same order as the single-bed final sum.
 __global__ void __launch_bounds__(1024)
     batch_final_kernel(const double* __restrict__ part, const int64_t* __restrict__ begin,
                        const int32_t* __restrict__ count, double* __restrict__ out) {
   __shared__ double sm[1024][4];
   const int bed = blockIdx.x;
-  const double* p = part + 4 * (begin[bed] / kSweepThreads);
+  const double* p = part + 4 * kWarpsPerBlock * (begin[bed] / kSweepThreads);
   const int64_t nblocks = ((int64_t)count[bed] + kSweepThreads - 1) / kSweepThreads;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t b = threadIdx.x; b < nblocks; b += 1024)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[j] += p[4 * b + j];
+    for (int j = 0; j < 4; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < kWarpsPerBlock; ++k) v += p[4 * (b * kWarpsPerBlock + k) + j];
+      acc[j] += v;
+    }
 #pragma unroll
   for (int j = 0; j < 4; ++j) sm[threadIdx.x][j] = acc[j];
   __syncthreads();

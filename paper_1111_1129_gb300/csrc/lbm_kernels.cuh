@@ -191,22 +191,97 @@ __device__ __forceinline__ void collide(C g[19], const Coef<C>& k, C alpha, C& r
   u_out[2] = uz;
 }
 
-// Fixed-order block reduction of 4 doubles; thread 0 writes out[0..3].
-__device__ __forceinline__ void block_sum4(double v[4], double* out) {
-  __shared__ double sm[kSweepThreads / 32][4];
+// ---- the flux reduction --------------------------------------------------------
+// The reducing step sums rho and u over its cells.  FP64 adds issue at 1/64
+// of the FP32 rate on GB300, and a shuffle tree costs every lane 20 of them
+// per cell: in FP64 the reduction made a reducing step of the 16-bit forms
+// 2.4x as long as a plain one.  Instead each cell's rho - 1 and u are turned
+// into int64 fixed point in units of 2^-60 (exact for |x| >= 2^-37 in FP32
+// and |x| >= 2^-8 in FP64; smaller values round to the unit, error below
+// 2^-61 per cell) and summed exactly per warp; each warp sum becomes FP64 once.  A warp holding
+// a value of magnitude >= 1/4, a NaN or an infinity sums in FP64 instead, so
+// such values (NaN included) still reach the result.  Warp sums are combined
+// in warp order, then over blocks in a fixed order: run-to-run identical.
+constexpr int kWarpsPerBlock = kSweepThreads / 32;
+
+__device__ __forceinline__ int64_t fixed60(float x) {   // |x| < 1/4
+  const uint32_t b = __float_as_uint(x);
+  const int e = (int)((b >> 23) & 0xffu);
+  if (e == 0) return 0;
+  const int64_t m = (int64_t)((b & 0x7fffffu) | 0x800000u);
+  const int s = e - 90;   // x = m 2^(e - 150) = m 2^s units
+  const int64_t v = s >= 0 ? (m << s) : (s > -25 ? ((m >> (-s - 1)) + 1) >> 1 : 0);
+  return (b >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ int64_t fixed60(double x) {   // |x| < 1/4
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ffu);
+  if (e == 0) return 0;
+  const int64_t m = (int64_t)((b & 0xfffffffffffffull) | (1ull << 52));
+  const int s = e - 1015;   // x = m 2^(e - 1075) = m 2^s units
+  const int64_t v = s >= 0 ? (m << s) : (s > -54 ? ((m >> (-s - 1)) + 1) >> 1 : 0);
+  return (b >> 63) ? -v : v;
+}
+
+// Warp sums of the cell's moments; lane 0 receives w[0] = sum rho (or
+// sum (rho - 1) for the shifted forms, whose rho is already rho - 1) and
+// w[1..3] = sum u.  Every lane of the warp must call it.
+template <class C, bool SHIFTED>
+__device__ __forceinline__ void warp_flux_sums(bool live, C rho, const C u[3], double w[4]) {
+  const C v[4] = {live ? (SHIFTED ? rho : rho - C(1)) : C(0), live ? u[0] : C(0),
+                  live ? u[1] : C(0), live ? u[2] : C(0)};
+  bool ok = true;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
+  for (int j = 0; j < 4; ++j) ok &= fabs(v[j]) < C(0.25);
+  int cnt = live && !SHIFTED ? 1 : 0;
+  if (__all_sync(0xffffffffu, ok)) {
+    int64_t s[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0)
+    for (int j = 0; j < 4; ++j) s[j] = fixed60(v[j]);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) sm[warp][j] = v[j];
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s[j] += __shfl_down_sync(0xffffffffu, s[j], o);
+      cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = (double)s[j] * 0x1p-60;
+  } else {
+    w[0] = live ? (SHIFTED ? (double)rho : (double)rho - 1.0) : 0.0;
+#pragma unroll
+    for (int j = 1; j < 4; ++j) w[j] = (double)v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] += __shfl_down_sync(0xffffffffu, w[j], o);
+      cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    }
+  }
+  w[0] += (double)cnt;
+}
+
+// Writes a warp's sums to its own slot: out[4 * (block * kWarpsPerBlock + warp) + j].
+__device__ __forceinline__ void store_warp_sums(const double w[4], double* partials) {
+  if ((threadIdx.x & 31) == 0) {
+    double* o = partials + 4 * ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[j] = w[j];
+  }
+}
+
+// Combines the block's warp sums in warp order into out[0..3] (the value
+// final_sum_kernel forms from store_warp_sums slots); has a block barrier.
+__device__ __forceinline__ void store_block_sums(const double w[4], double* out) {
+  __shared__ double sm[kWarpsPerBlock][4];
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sm[threadIdx.x >> 5][j] = w[j];
   __syncthreads();
   if (threadIdx.x < 4) {
     double acc = 0.0;
 #pragma unroll
-    for (int w = 0; w < kSweepThreads / 32; ++w) acc += sm[w][threadIdx.x];
+    for (int k = 0; k < kWarpsPerBlock; ++k) acc += sm[k][threadIdx.x];
     out[threadIdx.x] = acc;
   }
 }
@@ -238,30 +313,46 @@ constexpr int sweep_min_blocks() {
   return PREC == LBM_F64 ? 1 : LBM_SWEEP_MIN_BLOCKS;
 }
 
-template <int PREC, bool DAMPED, bool REDUCE>
-__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<PREC>())
+// RED: 0 no reduction; 1 warp sums into per-warp slots (no block barrier);
+// 2 block sums into per-block slots.  Both give the same final sums.
+enum { kNoReduce = 0, kWarpSums = 1, kBlockSums = 2 };
+
+// Resident blocks per SM the reducing variants of the FP32 and 16-bit
+// forms are fitted to: 4 keeps them at the plain variant's 64 registers
+// (1024x256x256 bed: FP16 reducing step 1.00 ms against 1.19 ms at the 72
+// registers the compiler picks unconstrained; a plain step takes 0.86 ms).
+#ifndef LBM_RED_MIN_BLOCKS
+#define LBM_RED_MIN_BLOCKS 4
+#endif
+
+template <int PREC, int RED>
+constexpr int sweep_launch_min_blocks() {
+  return RED != kNoReduce && PREC != LBM_F64 && PREC != LBM_F64X ? LBM_RED_MIN_BLOCKS
+                                                                 : sweep_min_blocks<PREC>();
+}
+
+template <int PREC, bool DAMPED, int RED>
+__global__ void __launch_bounds__(kSweepThreads, sweep_launch_min_blocks<PREC, RED>())
     sweep_kernel(const typename Form<PREC>::S* __restrict__ src,
                  typename Form<PREC>::S* __restrict__ dst, const int32_t* __restrict__ adj,
                  int32_t n, Coef<typename Form<PREC>::C> k,
                  const typename Form<PREC>::C* __restrict__ alpha, double* __restrict__ partials) {
   using C = typename Form<PREC>::C;
   const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
-  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  C rho = C(0), u[3] = {C(0), C(0), C(0)};
   if (i < n) {
     C g[19];
     gather<PREC>(src, adj, n, i, k.inv_scale, g);
-    C rho, u[3];
     collide<C, DAMPED>(g, k, DAMPED ? alpha[i] : C(0), rho, u);
 #pragma unroll
     for (int q = 0; q < 19; ++q) store_stream<PREC>(dst + q * n + i, encode<PREC>(g[q], k.scale));
-    if (REDUCE) {
-      red[0] = (double)rho;
-      red[1] = (double)u[0];
-      red[2] = (double)u[1];
-      red[3] = (double)u[2];
-    }
   }
-  if (REDUCE) block_sum4(red, partials + 4 * (int64_t)blockIdx.x);
+  if constexpr (RED != kNoReduce) {
+    double w[4];
+    warp_flux_sums<C, Form<PREC>::kShifted>(i < n, rho, u, w);
+    if constexpr (RED == kWarpSums) store_warp_sums(w, partials);
+    else store_block_sums(w, partials + 4 * (int64_t)blockIdx.x);
+  }
 }
 
 // Per-cell moments of the collision that a step from `src` performs.
@@ -284,14 +375,21 @@ __global__ void __launch_bounds__(kSweepThreads)
   u_out[2 * (int64_t)n + i] = (double)u[2];
 }
 
-// Final fixed-order sum of the block partials: out[j] = sum_b part[4 b + j].
+// Final fixed-order sum of the partials: out[j] = sum_b block_b[j], where
+// block b's value is the sum, in slot order, of its `per_block` slots
+// part[4 (b per_block + k) + j] (per_block = 1 for per-block partials).
 __global__ void __launch_bounds__(1024)
-    final_sum_kernel(const double* __restrict__ part, int64_t nblocks, double* out) {
+    final_sum_kernel(const double* __restrict__ part, int64_t nblocks, int per_block,
+                     double* out) {
   __shared__ double sm[1024][4];
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t b = threadIdx.x; b < nblocks; b += 1024)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[j] += part[4 * b + j];
+    for (int j = 0; j < 4; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < per_block; ++k) v += part[4 * (b * per_block + k) + j];
+      acc[j] += v;
+    }
 #pragma unroll
   for (int j = 0; j < 4; ++j) sm[threadIdx.x][j] = acc[j];
   __syncthreads();

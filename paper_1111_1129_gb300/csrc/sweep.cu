@@ -119,11 +119,11 @@ int launch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const dou
     const bool last = reduce_last && t == n_steps - 1;
     if (n > 0) {
       if (alpha) {
-        if (last) sweep_kernel<PREC, true, true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, st->partials);
-        else sweep_kernel<PREC, true, false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, st->partials);
+        if (last) sweep_kernel<PREC, true, kWarpSums><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, st->partials);
+        else sweep_kernel<PREC, true, kNoReduce><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, st->partials);
       } else {
-        if (last) sweep_kernel<PREC, false, true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, st->partials);
-        else sweep_kernel<PREC, false, false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, st->partials);
+        if (last) sweep_kernel<PREC, false, kWarpSums><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, st->partials);
+        else sweep_kernel<PREC, false, kNoReduce><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, st->partials);
       }
     }
     st->cur ^= 1;
@@ -315,7 +315,8 @@ extern "C" int lbm_state_create(const lbm_sparse* sp, int32_t precision, int32_t
   const size_t bytes = storage_bytes(precision) * 19 * (size_t)(n > 0 ? n : 1);
   bool ok = cudaMalloc(&st->buf[0], bytes) == cudaSuccess &&
             cudaMalloc(&st->buf[1], bytes) == cudaSuccess &&
-            cudaMalloc(&st->partials, sizeof(double) * 4 * st->nblocks) == cudaSuccess &&
+            cudaMalloc(&st->partials, sizeof(double) * 4 * kWarpsPerBlock * st->nblocks) ==
+                cudaSuccess &&
             cudaMalloc(&st->red_dev, sizeof(double) * 4) == cudaSuccess &&
             cudaMallocHost(&st->red_host, sizeof(double) * 4) == cudaSuccess &&
             cudaEventCreateWithFlags(&st->done, cudaEventDisableTiming) == cudaSuccess;
@@ -422,7 +423,8 @@ extern "C" int lbm_reduce_flux(lbm_state* st, int32_t axis, double* mass_out, do
   const cudaStream_t stream = st->sp->stream;
   const int64_t n = st->sp->n;
   if (n > 0) {
-    final_sum_kernel<<<1, 1024, 0, stream>>>(st->partials, st->nblocks, st->red_dev);
+    final_sum_kernel<<<1, 1024, 0, stream>>>(st->partials, st->nblocks, kWarpsPerBlock,
+                                             st->red_dev);
     LBM_CUDA_TRY(cudaGetLastError());
     LBM_CUDA_TRY(cudaMemcpyAsync(st->red_host, st->red_dev, sizeof(double) * 4,
                                  cudaMemcpyDeviceToHost, stream));
@@ -539,12 +541,12 @@ extern "C" int lbm_step_f64_noalloc(const double* f_src_dev, double* f_dst_dev,
   const int64_t nblocks = (n_fluid + kSweepThreads - 1) / kSweepThreads;
   const Coef<double> k = make_coef<double>(omega_plus, omega_minus, force, 0);
   if (alpha_dev)
-    sweep_kernel<LBM_F64, true, true><<<(unsigned)nblocks, kSweepThreads, 0, stream>>>(
+    sweep_kernel<LBM_F64, true, kBlockSums><<<(unsigned)nblocks, kSweepThreads, 0, stream>>>(
         f_src_dev, f_dst_dev, adj_dev, n, k, alpha_dev, partials);
   else
-    sweep_kernel<LBM_F64, false, true><<<(unsigned)nblocks, kSweepThreads, 0, stream>>>(
+    sweep_kernel<LBM_F64, false, kBlockSums><<<(unsigned)nblocks, kSweepThreads, 0, stream>>>(
         f_src_dev, f_dst_dev, adj_dev, n, k, nullptr, partials);
-  final_sum_kernel<<<1, 1024, 0, stream>>>(partials, nblocks, sums_dev);
+  final_sum_kernel<<<1, 1024, 0, stream>>>(partials, nblocks, 1, sums_dev);
   LBM_CUDA_TRY(cudaGetLastError());
   return LBM_OK;
 }

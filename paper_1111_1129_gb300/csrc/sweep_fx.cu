@@ -69,17 +69,19 @@ __device__ __forceinline__ int64_t fxmul(int64_t x, int64_t c63) { return __mul6
 #ifndef LBM_FX_MIN_BLOCKS
 #define LBM_FX_MIN_BLOCKS 3
 #endif
+#ifndef LBM_FX_RED_MIN_BLOCKS
+#define LBM_FX_RED_MIN_BLOCKS 2
+#endif
 
-// Block sums of rho and u for the flux reduction.  A cell on the fixed-point
+// Warp sums of rho and u for the flux reduction.  A cell on the fixed-point
 // path gives exact int64 moments in units U (rho - 1 below 2^57.4 and u
 // below 2^56 in magnitude, so a warp's sum stays below 2^63); they are summed
 // exactly per warp and converted to FP64 once per warp.  A cell that took
 // the IEEE path gives FP64 rho and u, summed only in warps that have one.
-// The per-warp values are then added in warp order: the result is
-// deterministic and rounds once per warp instead of once per cell.
-__device__ __forceinline__ void fx_block_sum(int64_t iv[4], int nfix, double dv[4], bool ieee,
-                                             double* out) {
-  __shared__ double sm[kSweepThreads / 32][4];
+// Each warp writes its own slot (no block barrier); the final sum combines
+// them in warp order, then over blocks in a fixed order.
+__device__ __forceinline__ void fx_warp_sums(int64_t iv[4], int nfix, double dv[4], bool ieee,
+                                             double* partials) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -92,25 +94,17 @@ __device__ __forceinline__ void fx_block_sum(int64_t iv[4], int nfix, double dv[
 #pragma unroll
       for (int j = 0; j < 4; ++j) dv[j] += __shfl_down_sync(0xffffffffu, dv[j], o);
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    sm[warp][0] = ((double)nfix + (double)iv[0] * 0x1p-58) + dv[0];
+  double w[4];
+  w[0] = ((double)nfix + (double)iv[0] * 0x1p-58) + dv[0];
 #pragma unroll
-    for (int j = 1; j < 4; ++j) sm[warp][j] = (double)iv[j] * 0x1p-58 + dv[j];
-  }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double acc = 0.0;
-#pragma unroll
-    for (int w = 0; w < kSweepThreads / 32; ++w) acc += sm[w][threadIdx.x];
-    out[threadIdx.x] = acc;
-  }
+  for (int j = 1; j < 4; ++j) w[j] = (double)iv[j] * 0x1p-58 + dv[j];
+  store_warp_sums(w, partials);
 }
 
 // HP_POW2: (1 - w+)/2 is +-2^-k (w+ = 1.25, 1.5, 0.75, ...), so the nine
 // even-part products are shifts.
 template <bool REDUCE, bool HP_POW2>
-__global__ void __launch_bounds__(kSweepThreads, REDUCE ? 2 : LBM_FX_MIN_BLOCKS)
+__global__ void __launch_bounds__(kSweepThreads, REDUCE ? LBM_FX_RED_MIN_BLOCKS : LBM_FX_MIN_BLOCKS)
     sweep_fx_kernel(const double* __restrict__ src, double* __restrict__ dst,
                     const int32_t* __restrict__ adj, int32_t n, FxCoef k, Coef<double> kd,
                     double* __restrict__ partials) {
@@ -237,7 +231,7 @@ __global__ void __launch_bounds__(kSweepThreads, REDUCE ? 2 : LBM_FX_MIN_BLOCKS)
       }
     }
   }
-  if (REDUCE) fx_block_sum(ired, nfix, red, i < n && nfix == 0, partials + 4 * (int64_t)blockIdx.x);
+  if (REDUCE) fx_warp_sums(ired, nfix, red, i < n && nfix == 0, partials);
 }
 
 int64_t c63(double c) { return (int64_t)std::llround(c * 0x1p63); }
