@@ -12,6 +12,7 @@ constexpr uint32_t kMagicSparse = 0x4C53504Bu;
 constexpr uint32_t kMagicState = 0x4C535354u;
 constexpr uint32_t kMagicAdjoint = 0x4C53414Du;
 constexpr int kSweepThreads = 256;
+constexpr int kWarpsPerBlock = kSweepThreads / 32;
 
 // Records a message for lbm_last_error() and returns `status`.
 int fail(int status, const char* fmt, ...);
@@ -278,7 +279,7 @@ struct lbm_state {
   void* buf[2];        // PDF grids, [19 * n] elements of the storage type
   int cur;             // index of the grid holding the current PDFs
   void* alpha;         // [n] damping in the arithmetic precision, or nullptr
-  double* partials;    // [nblocks * 4] FP64 block sums of the last step
+  double* partials;    // [nblocks * kWarpsPerBlock * 4] FP64 warp sums of the last step
   int64_t nblocks;
   double* red_dev;     // [4] final sums
   double* red_host;    // [4] pinned
@@ -298,7 +299,7 @@ size_t storage_bytes(int prec);   // bytes per stored PDF of a precision form
 size_t compute_bytes(int prec);   // bytes of the arithmetic type of a form
 bool is_shifted(int prec);        // stores f - w_q rather than f
 // Fixed-point FP64-storage sweep (sweep_fx.cu), undamped: n_steps launches
-// on `stream`; the last one writes the block sums when reduce_last is set.
+// on `stream`; the last one writes the warp sums when reduce_last is set.
 int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3],
                     cudaStream_t stream, bool reduce_last);
 bool valid_state(const lbm_state* st);

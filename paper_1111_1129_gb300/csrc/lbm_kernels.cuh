@@ -202,8 +202,6 @@ __device__ __forceinline__ void collide(C g[19], const Coef<C>& k, C alpha, C& r
 // a value of magnitude >= 1/4, a NaN or an infinity sums in FP64 instead, so
 // such values (NaN included) still reach the result.  Warp sums are combined
 // in warp order, then over blocks in a fixed order: run-to-run identical.
-constexpr int kWarpsPerBlock = kSweepThreads / 32;
-
 __device__ __forceinline__ int64_t fixed60(float x) {   // |x| < 1/4
   const uint32_t b = __float_as_uint(x);
   const int e = (int)((b >> 23) & 0xffu);

@@ -64,7 +64,7 @@ __device__ __forceinline__ int64_t fxmul(int64_t x, int64_t c63) { return __mul6
 // Resident blocks of 256 threads per SM the register budget is fitted to:
 // on the 1024x256x256 bed 3 (80 registers) beat 2 (120 registers) by 15%
 // and 4 (64 registers, heavy spills) by 5%.  The reducing variant, which
-// runs once per lbm_step call and also carries the block sums, is fitted
+// runs once per lbm_step call and also carries the warp sums, is fitted
 // to 2: without spills it takes 2.46 ms per launch there against 2.69 ms.
 #ifndef LBM_FX_MIN_BLOCKS
 #define LBM_FX_MIN_BLOCKS 3
