@@ -67,10 +67,13 @@ def test_wait_with_a_time_limit_reports_timeout_and_recovers():
     lat.close()
 
 
-def test_non_finite_state_is_reported():
+@pytest.mark.parametrize("precision", ["f64", "f64x", "f32s", "f16s"])
+def test_non_finite_state_is_reported(precision):
+    """A NaN must survive the reduction's fixed-point warp sums (the warp
+    holding it sums in FP64) and be reported."""
     bed = inputs.bed_small(0)
     lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "lex", periodic=bed.periodic)
-    st = LBMState(lat, "f64")
+    st = LBMState(lat, precision, 22)
     f = st.get_pdfs()
     f[3, 17] = float("nan")
     st.set_pdfs(f)
@@ -92,3 +95,21 @@ def test_errors_leave_a_readable_message_per_thread():
     t.start()
     t.join()
     assert seen == [""]
+
+
+def test_allocation_failure_is_reported_and_leaves_the_state_usable():
+    """An adjoint whose checkpoints would need petabytes: the device refuses
+    the allocation at once (nothing is consumed), the call returns
+    LBM_ENOMEM with a message, and the state steps on normally."""
+    bed = inputs.bed_small(0)
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "lex", periodic=bed.periodic)
+    st = LBMState(lat, "f64")
+    with pytest.raises(capi.LbmError) as ei:
+        capi.lbm_adjoint_create(st.handle, 2 ** 31 - 1, 1)
+    assert ei.value.status == capi.LBM_ENOMEM
+    assert "checkpoints" in str(ei.value)
+    st.step(10, WP, WM, (0.0, 0.0, 1e-6))
+    mass, flux = st.reduce_flux(2)
+    assert abs(mass - lat.n) < 1e-12 * lat.n and flux > 0
+    st.close()
+    lat.close()
