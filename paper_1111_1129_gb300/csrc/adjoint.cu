@@ -102,9 +102,14 @@ __device__ __forceinline__ int axis_component(int q, int axis) {
   return axis == 0 ? cx(q) : (axis == 1 ? cy(q) : cz(q));
 }
 
-// Block-sum 4 doubles and add them to acc[4] (each block owns its slot;
+// Block-sum 4 values and add them to acc[4] (each block owns its slot;
 // launches on one stream are ordered, so the accumulation is race free).
-__device__ __forceinline__ void block_accumulate4(double v[4], double* acc, bool assign) {
+// The warp level sums in the arithmetic precision T of the values: FP64
+// adds issue at 1/64 of the FP32 rate on GB300, and a shuffle tree costs
+// every lane 20 of them per cell, most of an FP32 adjoint step.  Warp sums
+// then accumulate in FP64.
+template <class T>
+__device__ __forceinline__ void block_accumulate4(T v[4], double* acc, bool assign) {
   __shared__ double sm[kSweepThreads / 32][4];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
@@ -113,7 +118,7 @@ __device__ __forceinline__ void block_accumulate4(double v[4], double* acc, bool
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) sm[warp][j] = v[j];
+    for (int j = 0; j < 4; ++j) sm[warp][j] = (double)v[j];
   __syncthreads();
   if (threadIdx.x < 4) {
     double s = 0.0;
@@ -165,7 +170,7 @@ __global__ void __launch_bounds__(kSweepThreads)
                         double* __restrict__ dalpha) {
   using C = typename Form<PREC>::C;
   const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
-  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  C red[4] = {C(0), C(0), C(0), C(0)};
   if (i < n) {
     int32_t idx[18];
 #pragma unroll
@@ -224,9 +229,9 @@ __global__ void __launch_bounds__(kSweepThreads)
     LBM_ADJ_PAIR(8, Gy - Gz)
 #undef LBM_ADJ_PAIR
     const C hs = C(0.5) * s, three_src = C(3) * a.src;
-    red[0] = (double)(hs * Gx + three_src * M1x);
-    red[1] = (double)(hs * Gy + three_src * M1y);
-    red[2] = (double)(hs * Gz + three_src * M1z);
+    red[0] = hs * Gx + three_src * M1x;
+    red[1] = hs * Gy + three_src * M1y;
+    red[2] = hs * Gz + three_src * M1z;
     const C Gu = Gx * u[0] + Gy * u[1] + Gz * u[2];
     const C M1u = M1x * u[0] + M1y * u[1] + M1z * u[2];
     dalpha[i] += (double)(-hs * Gu - three_src * M1u);
