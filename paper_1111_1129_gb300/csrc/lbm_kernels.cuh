@@ -292,7 +292,7 @@ __device__ __forceinline__ void gather(const typename Form<PREC>::S* __restrict_
                                        typename Form<PREC>::C g[19]) {
   int32_t idx[18];
 #pragma unroll
-  for (int q = 0; q < 18; ++q) idx[q] = __ldcs(adj + q * n + i);
+  for (int q = 0; q < 18; ++q) idx[q] = __ldg(adj + q * n + i);
   g[0] = decode<PREC>(load_ro<PREC>(src + i), inv_scale);
 #pragma unroll
   for (int q = 1; q < 19; ++q) g[q] = decode<PREC>(load_ro<PREC>(src + idx[q - 1]), inv_scale);

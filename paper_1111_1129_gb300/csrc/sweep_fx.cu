@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kSweepThreads, REDUCE ? LBM_FX_RED_MIN_BLOCKS 
   if (i < n) {
     int32_t idx[18];
 #pragma unroll
-    for (int q = 0; q < 18; ++q) idx[q] = __ldcs(adj + q * n + i);
+    for (int q = 0; q < 18; ++q) idx[q] = __ldg(adj + q * n + i);
     int64_t b[19];
     b[0] = __double_as_longlong(__ldg(src + i));
 #pragma unroll
