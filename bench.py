@@ -50,7 +50,7 @@ BYTES_PER_LUP = {"f64": 19 * 8 * 2 + 18 * 4, "f64x": 19 * 8 * 2 + 18 * 4,
 # The roofline's `traffic` multiplies them by the benchmark's cells.  Drop an
 # entry when its kernel changes.
 MEASURED_DRAM_BYTES_PER_LUP = {
-    ("large", "f64x"): 382.7,
+    ("large", "f64x"): 382.7, ("large", "f32s"): 230.1, ("large", "f16s"): 152.9,
 }
 STORAGE = {"f64": "f64", "f64x": "f64", "f32": "f32", "f32s": "f32 (f - w)",
            "f16s": "f16 ((f - w) 2^k)", "bf16s": "bf16 ((f - w) 2^k)"}

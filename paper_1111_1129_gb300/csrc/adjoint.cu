@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kSweepThreads)
   if (i < n) {
     int32_t idx[18];
 #pragma unroll
-    for (int q = 0; q < 18; ++q) idx[q] = __ldcs(adj + q * n + i);
+    for (int q = 0; q < 18; ++q) idx[q] = __ldg(adj + q * n + i);
     // all 36 pulls of the cell are independent: issue them back to back
     C lf[19], g[19];
     lf[0] = lam_in[i];
