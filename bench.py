@@ -44,13 +44,15 @@ BYTES_PER_LUP = {"f64": 19 * 8 * 2 + 18 * 4, "f64x": 19 * 8 * 2 + 18 * 4,
                  "f32s": 19 * 4 * 2 + 18 * 4, "f16s": 19 * 2 * 2 + 18 * 4,
                  "bf16s": 19 * 2 * 2 + 18 * 4}
 # DRAM bytes (read + write) per fluid update of one sweep launch, measured by
-# ncu per (workload, form): the full-size bed in one 1-pass capture
-# (profiles/sweep_f64x_f32s_f16s_bed1024x256x256_dram.md), the 256x128x128
-# bed in the --set full captures (profiles/sweep_*_bed256x128x128_ncu.md).
-# The roofline's `traffic` multiplies them by the benchmark's cells.  Drop an
+# ncu per (workload, form, ordering) on the full-size bed in one 1-pass
+# capture (profiles/sweep_f64x_f32s_f16s_bed1024x256x256_dram.md).  The
+# roofline's `traffic` multiplies them by the benchmark's cells.  Drop an
 # entry when its kernel changes.
 MEASURED_DRAM_BYTES_PER_LUP = {
-    ("large", "f64x"): 382.7, ("large", "f32s"): 230.1, ("large", "f16s"): 152.9,
+    ("large", "f64x", "lex"): 379.0, ("large", "f32s", "lex"): 223.1,
+    ("large", "f16s", "lex"): 147.4,
+    ("large", "f64x", "blocked"): 382.7, ("large", "f32s", "blocked"): 230.1,
+    ("large", "f16s", "blocked"): 152.9,
 }
 STORAGE = {"f64": "f64", "f64x": "f64", "f32": "f32", "f32s": "f32 (f - w)",
            "f16s": "f16 ((f - w) 2^k)", "bf16s": "bf16 ((f - w) 2^k)"}
@@ -303,7 +305,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": (MEASURED_DRAM_BYTES_PER_LUP[key] * n
-                                 if (key := (args.workload, args.precision))
+                                 if (key := (args.workload, args.precision, args.ordering))
                                  in MEASURED_DRAM_BYTES_PER_LUP else None),
                      "bytes_per_lup": bpl, "peak_kind": peak_kind,
                      "kernel": "sweep_fx_kernel" if args.precision == "f64x"
@@ -311,7 +313,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "MFLUP/s",
                 "h2d_bytes_per_step": (bed.flags.nbytes + 24) / args.steps,
                 "d2h_bytes_per_step": 32 / args.steps},
-        "gpu_launches": args.steps + 1,
+        "gpu_launches": args.steps + 2,
         "clocks": clocks.summary(),
         "result": {"mass": mass, "flux": flux, "e2e_flux": e2e_flux},
     }
@@ -327,8 +329,8 @@ def run_ours(args):
 
 
 def _extras(lat, bed, wm, args):
-    """Short labelled runs: the other orderings (FP64) and the other storage
-    forms (8^3 blocked)."""
+    """Short labelled runs: the other orderings (in the benchmark's form) and
+    the other storage forms (in the benchmark's ordering)."""
     import torch
 
     from paper_1111_1129_gb300 import LBMState, SparseLattice
@@ -622,7 +624,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=list(WORKLOADS))
-    ap.add_argument("--ordering", default="blocked", choices=["lex", "blocked", "morton1",
+    ap.add_argument("--ordering", default="lex", choices=["lex", "blocked", "morton1",
                                                                "morton2", "hilbert"])
     ap.add_argument("--precision", default="f64x", choices=list(BYTES_PER_LUP))
     ap.add_argument("--extra-steps", type=int, default=50)

@@ -391,7 +391,7 @@ int finish_sums(lbm_adjoint* ad) {
     for (int j = 0; j < 4; ++j) ad->red_host[j] = 0.0;
     return LBM_OK;
   }
-  final_sum_kernel<<<1, 1024, 0, stream>>>(ad->part, ad->st->nblocks, 1, ad->red_dev);
+  final_sum_kernel<<<1, 1024, 0, stream>>>(ad->part, ad->st->nblocks, ad->red_dev);
   LBM_CUDA_TRY(cudaGetLastError());
   LBM_CUDA_TRY(cudaMemcpyAsync(ad->red_host, ad->red_dev, 4 * sizeof(double),
                                cudaMemcpyDeviceToHost, stream));

@@ -279,7 +279,8 @@ struct lbm_state {
   void* buf[2];        // PDF grids, [19 * n] elements of the storage type
   int cur;             // index of the grid holding the current PDFs
   void* alpha;         // [n] damping in the arithmetic precision, or nullptr
-  double* partials;    // [nblocks * kWarpsPerBlock * 4] FP64 warp sums of the last step
+  double* partials;    // [nblocks * kWarpsPerBlock * 4] FP64 warp sums of the last step,
+                       // then [nblocks * 4] block values formed by lbm_reduce_flux
   int64_t nblocks;
   double* red_dev;     // [4] final sums
   double* red_host;    // [4] pinned

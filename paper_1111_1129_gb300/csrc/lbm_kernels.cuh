@@ -269,7 +269,8 @@ __device__ __forceinline__ void store_warp_sums(const double w[4], double* parti
 }
 
 // Combines the block's warp sums in warp order into out[0..3] (the value
-// final_sum_kernel forms from store_warp_sums slots); has a block barrier.
+// collapse_warp_sums_kernel forms from store_warp_sums slots); has a block
+// barrier.
 __device__ __forceinline__ void store_block_sums(const double w[4], double* out) {
   __shared__ double sm[kWarpsPerBlock][4];
   if ((threadIdx.x & 31) == 0)
@@ -373,21 +374,33 @@ __global__ void __launch_bounds__(kSweepThreads)
   u_out[2 * (int64_t)n + i] = (double)u[2];
 }
 
-// Final fixed-order sum of the partials: out[j] = sum_b block_b[j], where
-// block b's value is the sum, in slot order, of its `per_block` slots
-// part[4 (b per_block + k) + j] (per_block = 1 for per-block partials).
+// Block values from per-warp slots, one thread per block: blocks[4 b + j] =
+// sum over the block's kWarpsPerBlock slots, in slot order (the value
+// store_block_sums forms inside a block).  Spreads the reading of the slots
+// over the GPU; final_sum_kernel then sums the blocks.
+__global__ void __launch_bounds__(256)
+    collapse_warp_sums_kernel(const double* __restrict__ part, int64_t nblocks,
+                              double* __restrict__ blocks) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblocks) return;
+  const double* p = part + 4 * kWarpsPerBlock * b;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < kWarpsPerBlock; ++k) v += p[4 * k + j];
+    blocks[4 * b + j] = v;
+  }
+}
+
+// Final fixed-order sum of the block values: out[j] = sum_b part[4 b + j].
 __global__ void __launch_bounds__(1024)
-    final_sum_kernel(const double* __restrict__ part, int64_t nblocks, int per_block,
-                     double* out) {
+    final_sum_kernel(const double* __restrict__ part, int64_t nblocks, double* out) {
   __shared__ double sm[1024][4];
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t b = threadIdx.x; b < nblocks; b += 1024)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      double v = 0.0;
-      for (int k = 0; k < per_block; ++k) v += part[4 * (b * per_block + k) + j];
-      acc[j] += v;
-    }
+    for (int j = 0; j < 4; ++j) acc[j] += part[4 * b + j];
 #pragma unroll
   for (int j = 0; j < 4; ++j) sm[threadIdx.x][j] = acc[j];
   __syncthreads();

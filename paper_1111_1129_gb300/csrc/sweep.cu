@@ -315,7 +315,7 @@ extern "C" int lbm_state_create(const lbm_sparse* sp, int32_t precision, int32_t
   const size_t bytes = storage_bytes(precision) * 19 * (size_t)(n > 0 ? n : 1);
   bool ok = cudaMalloc(&st->buf[0], bytes) == cudaSuccess &&
             cudaMalloc(&st->buf[1], bytes) == cudaSuccess &&
-            cudaMalloc(&st->partials, sizeof(double) * 4 * kWarpsPerBlock * st->nblocks) ==
+            cudaMalloc(&st->partials, sizeof(double) * 4 * (kWarpsPerBlock + 1) * st->nblocks) ==
                 cudaSuccess &&
             cudaMalloc(&st->red_dev, sizeof(double) * 4) == cudaSuccess &&
             cudaMallocHost(&st->red_host, sizeof(double) * 4) == cudaSuccess &&
@@ -423,8 +423,10 @@ extern "C" int lbm_reduce_flux(lbm_state* st, int32_t axis, double* mass_out, do
   const cudaStream_t stream = st->sp->stream;
   const int64_t n = st->sp->n;
   if (n > 0) {
-    final_sum_kernel<<<1, 1024, 0, stream>>>(st->partials, st->nblocks, kWarpsPerBlock,
-                                             st->red_dev);
+    double* blocks = st->partials + 4 * kWarpsPerBlock * st->nblocks;
+    collapse_warp_sums_kernel<<<(unsigned)((st->nblocks + 255) / 256), 256, 0, stream>>>(
+        st->partials, st->nblocks, blocks);
+    final_sum_kernel<<<1, 1024, 0, stream>>>(blocks, st->nblocks, st->red_dev);
     LBM_CUDA_TRY(cudaGetLastError());
     LBM_CUDA_TRY(cudaMemcpyAsync(st->red_host, st->red_dev, sizeof(double) * 4,
                                  cudaMemcpyDeviceToHost, stream));
@@ -546,7 +548,7 @@ extern "C" int lbm_step_f64_noalloc(const double* f_src_dev, double* f_dst_dev,
   else
     sweep_kernel<LBM_F64, false, kBlockSums><<<(unsigned)nblocks, kSweepThreads, 0, stream>>>(
         f_src_dev, f_dst_dev, adj_dev, n, k, nullptr, partials);
-  final_sum_kernel<<<1, 1024, 0, stream>>>(partials, nblocks, 1, sums_dev);
+  final_sum_kernel<<<1, 1024, 0, stream>>>(partials, nblocks, sums_dev);
   LBM_CUDA_TRY(cudaGetLastError());
   return LBM_OK;
 }
