@@ -639,7 +639,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--ordering-study", action="store_true",
                     help="run the numbering-scheme study instead of the benchmark")
-    ap.add_argument("--study-forms", default="f64,f32s,f16s")
+    ap.add_argument("--study-forms", default="f64x,f32s,f16s")
     ap.add_argument("--adjoint-study", action="store_true",
                     help="time the checkpointed adjoint against the forward run")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
