@@ -198,10 +198,11 @@ __device__ __forceinline__ void collide(C g[19], const Coef<C>& k, C alpha, C& r
 // 2.4x as long as a plain one.  Instead each cell's rho - 1 and u are turned
 // into int64 fixed point in units of 2^-60 (exact for |x| >= 2^-37 in FP32
 // and |x| >= 2^-8 in FP64; smaller values round to the unit, error below
-// 2^-61 per cell) and summed exactly per warp; each warp sum becomes FP64 once.  A warp holding
-// a value of magnitude >= 1/4, a NaN or an infinity sums in FP64 instead, so
-// such values (NaN included) still reach the result.  Warp sums are combined
-// in warp order, then over blocks in a fixed order: run-to-run identical.
+// 2^-61 per cell) and summed exactly per warp; each warp sum becomes FP64
+// once.  A warp holding a value of magnitude >= 1/4, a NaN or an infinity
+// sums in FP64 instead, so such values (NaN included) still reach the
+// result.  Warp sums are combined in warp order, then over blocks in a
+// fixed order: run-to-run identical.
 __device__ __forceinline__ int64_t fixed60(float x) {   // |x| < 1/4
   const uint32_t b = __float_as_uint(x);
   const int e = (int)((b >> 23) & 0xffu);
