@@ -189,7 +189,7 @@ def run_reference(args):
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][0], "ordering": "dense full-array oracle",
-                   "precision": "f64", "cells_per_step": None},
+                   "precision": "f64", "fluid_cells_per_sample": n_fluid},
         "cpu_baseline": {"value": value, "unit": "MFLUP/s", "cores": cores, "kind": "oracle",
                          "sample": f"each step: 64x256x256 slab of the bed (x in [0,64), "
                                    f"periodic x, {n_fluid} fluid cells), ~3 s of oracle "
