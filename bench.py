@@ -64,10 +64,19 @@ ARITHMETIC_NOTE = {
             "round-off (parity 1e-12 vs the oracle) and conserve the stored mass exactly; "
             "cells outside the fast range use IEEE FP64",
     "f32": "FP32", "f32s": "FP32", "f16s": "FP32", "bf16s": "FP32"}
+# name: (label, input generator, flow axis).  The body force, 1e-6, points
+# along the tube.
 WORKLOADS = {
-    "large": ("packed bed 1024x256x256, tube D=250 along x, spheres r=8, seed 0", "bed_large"),
-    "medium": ("packed bed 256x128x128, tube D=122 along x, spheres r=8, seed 0", "bed_medium"),
+    "large": ("packed bed 1024x256x256, tube D=250 along x, spheres r=8, seed 0", "bed_large", 0),
+    "medium": ("packed bed 256x128x128, tube D=122 along x, spheres r=8, seed 0", "bed_medium", 0),
+    "small": ("packed bed 32x32x64, tube D=30 along z, spheres r=4, seed 0", "bed_small", 2),
 }
+
+
+def _flow(workload):
+    """(force, axis) of a workload."""
+    axis = WORKLOADS[workload][2]
+    return tuple(1e-6 if d == axis else 0.0 for d in range(3)), axis
 
 
 def _peaks():
@@ -142,28 +151,39 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def _oracle_sample(bed, budget_s: float, max_steps: int | None = None):
-    """The CPU oracle on a bounded slab of the bed (x in [0, 64), periodic
-    in x): returns (MFLUP/s, steps, fluid cells, cores, seconds)."""
+def _oracle_slab(bed):
+    """What the CPU oracle runs: a bed up to 64 cells long in x whole, with
+    its own boundaries, else the slab x in [0, 64), periodic in x (the tube
+    of the larger beds runs along x).  Returns (flags, periodic, label)."""
     import numpy as np
 
+    nz, ny, nx = bed.flags.shape
+    if nx <= 64:
+        return bed.flags, bed.periodic, f"the whole {nx}x{ny}x{nz} bed"
+    slab = np.ascontiguousarray(bed.flags[:, :, :64])
+    return slab, 1, f"64x{ny}x{nz} slab of the bed (x in [0,64), periodic x)"
+
+
+def _oracle_sample(bed, budget_s: float, force, max_steps: int | None = None):
+    """The CPU oracle on a bounded sample of the bed (_oracle_slab): returns
+    (MFLUP/s, steps, fluid cells, cores, seconds, label)."""
     import oracle
 
-    slab = np.ascontiguousarray(bed.flags[:, :, :64])
+    slab, periodic, label = _oracle_slab(bed)
     n_fluid = int((slab == 0).sum())
     wm = oracle.omega_minus(WP)
     f = oracle.rest_state(slab)
     t0 = time.perf_counter()
-    f, _, _, _ = oracle.run(slab, 1, WP, wm, FORCE, 1, f=f)
+    f, _, _, _ = oracle.run(slab, periodic, WP, wm, force, 1, f=f)
     one = time.perf_counter() - t0
     steps = max(1, int(budget_s / max(one, 1e-6)))
     if max_steps is not None:
         steps = min(steps, max_steps)
     t0 = time.perf_counter()
-    oracle.run(slab, 1, WP, wm, FORCE, steps, f=f)
+    oracle.run(slab, periodic, WP, wm, force, steps, f=f)
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return n_fluid * steps / dt / 1e6, steps, n_fluid, cores, dt
+    return n_fluid * steps / dt / 1e6, steps, n_fluid, cores, dt, label
 
 
 def run_reference(args):
@@ -172,13 +192,14 @@ def run_reference(args):
         return 0
     from paper_1111_1129_gb300 import inputs
     bed = getattr(inputs, WORKLOADS[args.workload][1])(0)
+    force, _ = _flow(args.workload)
     for _ in range(args.warmup):
-        _oracle_sample(bed, 0.5, max_steps=1)
+        _oracle_sample(bed, 0.5, force, max_steps=1)
     lups = 0.0
     dt = 0.0          # the oracle's own time steps; its per-sample set-up is not counted
     samples = []
     for _ in range(args.steps):
-        mflups, steps, n_fluid, cores, t = _oracle_sample(bed, 3.0)
+        mflups, steps, n_fluid, cores, t, label = _oracle_sample(bed, 3.0, force)
         lups += n_fluid * steps
         dt += t
         samples.append(steps)
@@ -191,9 +212,8 @@ def run_reference(args):
         "config": {"workload": WORKLOADS[args.workload][0], "ordering": "dense full-array oracle",
                    "precision": "f64", "fluid_cells_per_sample": n_fluid},
         "cpu_baseline": {"value": value, "unit": "MFLUP/s", "cores": cores, "kind": "oracle",
-                         "sample": f"each step: 64x256x256 slab of the bed (x in [0,64), "
-                                   f"periodic x, {n_fluid} fluid cells), ~3 s of oracle "
-                                   f"time steps ({samples[0]} steps in the first)"},
+                         "sample": f"each step: {label} ({n_fluid} fluid cells), ~3 s of "
+                                   f"oracle time steps ({samples[0]} steps in the first)"},
         "e2e": {"value": value, "unit": "MFLUP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -218,6 +238,7 @@ def run_ours(args):
     wm = omega_minus(WP)
     # weak scaling: each rank owns an independent bed (seed = rank)
     bed = getattr(inputs, WORKLOADS[args.workload][1])(rank)
+    force, axis = _flow(args.workload)
     flags_host = torch.from_numpy(bed.flags).pin_memory()
     stream = torch.cuda.current_stream()
 
@@ -229,16 +250,16 @@ def run_ours(args):
     lat = SparseLattice(flags_host.cuda(), args.ordering, (8, 8, 8), bed.periodic)
     n = lat.n
     st = LBMState(lat, args.precision)
-    st.step(args.warmup, WP, wm, FORCE)
-    st.reduce_flux(AXIS)
+    st.step(args.warmup, WP, wm, force)
+    st.reduce_flux(axis)
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
         barrier()
         ev0.record(stream)
-        st.step(args.steps, WP, wm, FORCE)
-        mass, flux = st.reduce_flux(AXIS)
+        st.step(args.steps, WP, wm, force)
+        mass, flux = st.reduce_flux(axis)
         ev1.record(stream)
         barrier()
     ms = ev0.elapsed_time(ev1)
@@ -264,8 +285,8 @@ def run_ours(args):
                                                      (8, 8, 8), bed.periodic),
                                   int(stream.cuda_stream))
     h_st = capi.lbm_state_create(h_lat, lbm_mod.PRECISIONS[args.precision], 0)
-    capi.lbm_step(h_st, args.steps, WP, wm, FORCE)
-    e2e_mass, e2e_flux = capi.lbm_reduce_flux(h_st, AXIS)
+    capi.lbm_step(h_st, args.steps, WP, wm, force)
+    e2e_mass, e2e_flux = capi.lbm_reduce_flux(h_st, axis)
     e2e_s = time.perf_counter() - t0
     capi.lbm_free(h_st)
     capi.lbm_free(h_lat)
@@ -278,16 +299,16 @@ def run_ours(args):
     extra = {}
     cpu = None
     if rank == 0 and world == 1 and not args.no_extra:
-        extra = _extras(lat, bed, wm, args)
+        extra = _extras(lat, bed, wm, args, force)
     if rank == 0 and world == 1 and not args.no_cpu:
-        mflups, steps_c, n_c, cores, dt = _oracle_sample(bed, args.cpu_seconds)
+        mflups, steps_c, n_c, cores, dt, label = _oracle_sample(bed, args.cpu_seconds, force)
         cpu = {"value": mflups, "unit": "MFLUP/s", "cores": cores, "kind": "oracle",
-               "sample": f"64x256x256 slab of the bed (x in [0,64), periodic x, {n_c} fluid "
-                         f"cells), {steps_c} FP64 steps of the dense full-array oracle "
-                         f"({dt:.1f} s)"}
+               "sample": f"{label} ({n_c} fluid cells), {steps_c} FP64 steps of the dense "
+                         f"full-array oracle ({dt:.1f} s)"}
     lat.close()
     peak, peak_kind = _peaks()
     bpl = BYTES_PER_LUP[args.precision]
+    ws = (2 * 19 * (bpl - 72) / 38 + 72) * n   # two PDF grids + adjacency, bytes
     achieved = bpl * n / (launch_ms * 1e-3) / 1e9
     line = {
         "metric": "MFLUP/s", "value": value, "unit": "MFLUP/s", "n_gpus": world,
@@ -297,10 +318,11 @@ def run_ours(args):
         "config": {"workload": WORKLOADS[args.workload][0], "fluid_cells_per_gpu": n, "ordering": f"{args.ordering}"
                    + (" 8^3" if args.ordering == "blocked" else ""),
                    "precision": args.precision, "storage": STORAGE[args.precision],
-                   "arithmetic": ARITHMETIC_NOTE[args.precision], "force": list(FORCE),
+                   "arithmetic": ARITHMETIC_NOTE[args.precision], "force": list(force),
                    "omega_plus": WP, "omega_minus": wm,
-                   "l2": "inputs larger than L2 (PDFs+adjacency ~%.1f GB)" % (
-                       (2 * 19 * (bpl - 72) / 38 + 72) * n / 1e9),
+                   "l2": ("inputs larger than L2 (PDFs+adjacency ~%.1f GB)" if ws > 129e6 else
+                          "inputs fit in L2 (PDFs+adjacency ~%.3f GB): an L2-bound rate, not an "
+                          "HBM one") % (ws / 1e9),
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
@@ -328,7 +350,7 @@ def run_ours(args):
     return 0
 
 
-def _extras(lat, bed, wm, args):
+def _extras(lat, bed, wm, args, force):
     """Short labelled runs: the other orderings (in the benchmark's form) and
     the other storage forms (in the benchmark's ordering)."""
     import torch
@@ -337,11 +359,11 @@ def _extras(lat, bed, wm, args):
 
     def timed(lattice, precision, steps, scale_exp=0):
         st = LBMState(lattice, precision, scale_exp)
-        st.step(3, WP, wm, FORCE)
+        st.step(3, WP, wm, force)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        st.step(steps, WP, wm, FORCE)
+        st.step(steps, WP, wm, force)
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
