@@ -64,12 +64,15 @@ ARITHMETIC_NOTE = {
             "round-off (parity 1e-12 vs the oracle) and conserve the stored mass exactly; "
             "cells outside the fast range use IEEE FP64",
     "f32": "FP32", "f32s": "FP32", "f16s": "FP32", "bf16s": "FP32"}
-# name: (label, input generator, flow axis).  The body force, 1e-6, points
-# along the tube.
+# name: (label, input generator, flow axis, tube radius).  The body force,
+# 1e-6, points along the tube.
 WORKLOADS = {
-    "large": ("packed bed 1024x256x256, tube D=250 along x, spheres r=8, seed 0", "bed_large", 0),
-    "medium": ("packed bed 256x128x128, tube D=122 along x, spheres r=8, seed 0", "bed_medium", 0),
-    "small": ("packed bed 32x32x64, tube D=30 along z, spheres r=4, seed 0", "bed_small", 2),
+    "large": ("packed bed 1024x256x256, tube D=250 along x, spheres r=8, seed 0", "bed_large",
+              0, 125.0),
+    "medium": ("packed bed 256x128x128, tube D=122 along x, spheres r=8, seed 0", "bed_medium",
+               0, 61.0),
+    "small": ("packed bed 32x32x64, tube D=30 along z, spheres r=4, seed 0", "bed_small", 2,
+              15.0),
 }
 
 
@@ -77,6 +80,12 @@ def _flow(workload):
     """(force, axis) of a workload."""
     axis = WORKLOADS[workload][2]
     return tuple(1e-6 if d == axis else 0.0 for d in range(3)), axis
+
+
+def _scale_exp(workload):
+    """Scale exponent of the 16-bit shifted forms for a workload's flow."""
+    from paper_1111_1129_gb300 import deviation_bound, shifted_scale_exp
+    return shifted_scale_exp(deviation_bound(1e-6, WORKLOADS[workload][3], WP))
 
 
 def _peaks():
@@ -249,7 +258,8 @@ def run_ours(args):
 
     lat = SparseLattice(flags_host.cuda(), args.ordering, (8, 8, 8), bed.periodic)
     n = lat.n
-    st = LBMState(lat, args.precision)
+    k16 = _scale_exp(args.workload)
+    st = LBMState(lat, args.precision, k16)
     st.step(args.warmup, WP, wm, force)
     st.reduce_flux(axis)
     barrier()
@@ -284,7 +294,7 @@ def run_ours(args):
                                   capi.make_ordering(lbm_mod.ORDERINGS[args.ordering],
                                                      (8, 8, 8), bed.periodic),
                                   int(stream.cuda_stream))
-    h_st = capi.lbm_state_create(h_lat, lbm_mod.PRECISIONS[args.precision], 0)
+    h_st = capi.lbm_state_create(h_lat, lbm_mod.PRECISIONS[args.precision], k16)
     capi.lbm_step(h_st, args.steps, WP, wm, force)
     e2e_mass, e2e_flux = capi.lbm_reduce_flux(h_st, axis)
     e2e_s = time.perf_counter() - t0
@@ -299,7 +309,7 @@ def run_ours(args):
     extra = {}
     cpu = None
     if rank == 0 and world == 1 and not args.no_extra:
-        extra = _extras(lat, bed, wm, args, force)
+        extra = _extras(lat, bed, wm, args, force, k16)
     if rank == 0 and world == 1 and not args.no_cpu:
         mflups, steps_c, n_c, cores, dt, label = _oracle_sample(bed, args.cpu_seconds, force)
         cpu = {"value": mflups, "unit": "MFLUP/s", "cores": cores, "kind": "oracle",
@@ -318,6 +328,7 @@ def run_ours(args):
         "config": {"workload": WORKLOADS[args.workload][0], "fluid_cells_per_gpu": n, "ordering": f"{args.ordering}"
                    + (" 8^3" if args.ordering == "blocked" else ""),
                    "precision": args.precision, "storage": STORAGE[args.precision],
+                   "scale_exp": k16 if args.precision in ("f16s", "bf16s") else None,
                    "arithmetic": ARITHMETIC_NOTE[args.precision], "force": list(force),
                    "omega_plus": WP, "omega_minus": wm,
                    "l2": ("inputs larger than L2 (PDFs+adjacency ~%.1f GB)" if ws > 129e6 else
@@ -350,7 +361,7 @@ def run_ours(args):
     return 0
 
 
-def _extras(lat, bed, wm, args, force):
+def _extras(lat, bed, wm, args, force, k16):
     """Short labelled runs: the other orderings (in the benchmark's form) and
     the other storage forms (in the benchmark's ordering)."""
     import torch
@@ -378,13 +389,13 @@ def _extras(lat, bed, wm, args, force):
         else:
             l2 = SparseLattice(torch.from_numpy(bed.flags).cuda(), name, (8, 8, 8), bed.periodic)
         orders[name + (" 8^3" if name == "blocked" else "")] = timed(l2, args.precision,
-                                                                    args.extra_steps)
+                                                                    args.extra_steps, k16)
         if l2 is not lat:
             l2.close()
     out[f"{args.precision}_by_ordering_mflups"] = orders
     forms = {}
-    for prec, k in (("f64", 0), ("f64x", 0), ("f32", 0), ("f32s", 0), ("f16s", 24),
-                    ("bf16s", 24)):
+    for prec, k in (("f64", 0), ("f64x", 0), ("f32", 0), ("f32s", 0), ("f16s", k16),
+                    ("bf16s", k16)):
         if prec != args.precision:
             forms[prec] = timed(lat, prec, args.extra_steps, k)
     out["by_storage_mflups"] = forms
