@@ -613,7 +613,7 @@ def run_ordering_study(args):
         lat = SparseLattice(flags, name, block, bed.periodic)
         row = {"ordering": name if name != "blocked" else f"blocked {block[0]}"}
         for prec in args.study_forms.split(","):
-            st = LBMState(lat, prec, 24)
+            st = LBMState(lat, prec, _scale_exp("large"))
             st.step(3, WP, wm, FORCE)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
