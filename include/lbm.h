@@ -186,8 +186,12 @@ int lbm_step(lbm_state* st, int32_t n_steps, double omega_plus, double omega_min
 
 /*
  * Mass and mean axial velocity of the most recent step's collision:
- * mass = sum_n rho_n and flux = (1/N) sum_n u_axis,n, both in FP64 with a
- * fixed summation order (run to run identical).  axis in {0,1,2}.
+ * mass = sum_n rho_n and flux = (1/N) sum_n u_axis,n, returned in FP64.
+ * Within each warp of 32 cells, rho - 1 and u are summed exactly as int64
+ * fixed point in units of 2^-60 (2^-58 for LBM_F64X); a warp holding a
+ * value of magnitude >= 1/4, NaN or Inf sums in FP64 instead.  Warp sums
+ * are added in FP64 in a fixed order, so results are run-to-run identical.
+ * axis in {0,1,2}.
  * Synchronises the stream (bounded by lbm_set_timeout).  Errors:
  * LBM_EINVAL (no step taken yet, bad axis), LBM_ENONFINITE, LBM_ETIMEOUT,
  * LBM_ECUDA.
