@@ -464,7 +464,7 @@ def run_adjoint_study(args):
     wm = omega_minus(WP)
     bed = inputs.bed_cube128(0)
     alpha_dense = inputs.alpha_field(bed.dims, seed=0)
-    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "blocked", (8, 8, 8), bed.periodic)
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), args.ordering, (8, 8, 8), bed.periodic)
     alpha = torch.from_numpy(alpha_dense.reshape(-1)[lat.cells().cpu().numpy()].copy()).cuda()
     K, stride, F = args.adjoint_steps, 45, (0.0, 0.0, 1e-6)
     out = {}
@@ -498,8 +498,8 @@ def run_adjoint_study(args):
         adj.close()
         st.close()
     line = {"study": "adjoint", "workload": "packed bed 128^3, tube D=126 along z, spheres r=6, "
-            "damping U[0,0.05)", "fluid_cells": lat.n, "steps": K, "checkpoint_stride": stride,
-            "forms": out}
+            "damping U[0,0.05)", "fluid_cells": lat.n, "ordering": args.ordering, "steps": K,
+            "checkpoint_stride": stride, "forms": out}
     lat.close()
     print(json.dumps(line), flush=True)
     return 0
@@ -519,7 +519,7 @@ def run_batch_study(args):
     wm = omega_minus(WP)
     beds, fz = inputs.batch_beds(256, 0)
     forces = [(0.0, 0.0, float(f)) for f in fz]
-    lats = [SparseLattice(torch.from_numpy(b.flags).cuda(), "blocked", (8, 8, 8), b.periodic)
+    lats = [SparseLattice(torch.from_numpy(b.flags).cuda(), args.ordering, (8, 8, 8), b.periodic)
             for b in beds]
     n_fluid = sum(l.n for l in lats)
     K = args.batch_steps
@@ -562,7 +562,7 @@ def run_batch_study(args):
     for l in lats:
         l.close()
     line = {"study": "batched beds", "n_beds": 256, "fluid_cells": n_fluid, "steps": K,
-            "precision": "f32s", "tuned": {"block": block, "cells_per_thread": cpt,
+            "ordering": args.ordering, "precision": "f32s", "tuned": {"block": block, "cells_per_thread": cpt,
                                            "candidate_ms_block_major": cand},
             **out, "speedup_vs_separate": out["batched_graph"]["mflups"] /
             out["separate_loops"]["mflups"],
