@@ -63,175 +63,238 @@ __device__ __forceinline__ int64_t fxmul(int64_t x, int64_t c63) { return __mul6
 
 // Resident blocks of 256 threads per SM the register budget is fitted to:
 // on the 1024x256x256 bed 3 (80 registers) beat 2 (120 registers) by 15%
-// and 4 (64 registers, heavy spills) by 5%.  The reducing variant, which
-// runs once per lbm_step call and also carries the warp sums, is fitted
-// to 2: without spills it takes 2.46 ms per launch there against 2.69 ms.
+// and 4 (64 registers, heavy spills) by 5%.  The reducing kernel, which
+// runs once per lbm_step call, is fitted to 3 as well: 2.07 ms per launch
+// there, against 1.84 ms for a plain step.
 #ifndef LBM_FX_MIN_BLOCKS
 #define LBM_FX_MIN_BLOCKS 3
 #endif
 #ifndef LBM_FX_RED_MIN_BLOCKS
-#define LBM_FX_RED_MIN_BLOCKS 2
+#define LBM_FX_RED_MIN_BLOCKS 3
 #endif
 
-// Warp sums of rho and u for the flux reduction.  A cell on the fixed-point
-// path gives exact int64 moments in units U (rho - 1 below 2^57.4 and u
-// below 2^56 in magnitude, so a warp's sum stays below 2^63); they are summed
-// exactly per warp and converted to FP64 once per warp.  A cell that took
-// the IEEE path gives FP64 rho and u, summed only in warps that have one.
-// Each warp writes its own slot (no block barrier); the final sum combines
-// them in warp order, then over blocks in a fixed order.
-__device__ __forceinline__ void fx_warp_sums(int64_t iv[4], int nfix, double dv[4], bool ieee,
-                                             double* partials) {
+// Warp sums of rho and u for the flux reduction, in two parts.  Cells on the
+// fixed-point path give exact int64 moments in units U (rho - 1 below
+// 2^57.4 and u below 2^56 in magnitude, so a warp's sum stays below 2^63);
+// they are summed exactly as soon as the moments are known, so nothing of
+// the reduction stays live through the collision, and lane 0 writes the
+// warp's slot.  Cells that took the IEEE path add their FP64 rho and u to
+// the slot afterwards, in warps that have one.  The final sum combines the
+// slots in warp order, then over blocks in a fixed order.
+__device__ __forceinline__ void fx_fixed_warp_sums(int64_t drho, int64_t ux, int64_t uy,
+                                                   int64_t uz, int nfix, double* partials) {
+  int64_t iv[4] = {drho, ux, uy, uz};
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) iv[j] += __shfl_down_sync(0xffffffffu, iv[j], o);
     nfix += __shfl_down_sync(0xffffffffu, nfix, o);
   }
-  if (__any_sync(0xffffffffu, ieee)) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) dv[j] += __shfl_down_sync(0xffffffffu, dv[j], o);
-  }
   double w[4];
-  w[0] = ((double)nfix + (double)iv[0] * 0x1p-58) + dv[0];
+  w[0] = (double)nfix + (double)iv[0] * 0x1p-58;
 #pragma unroll
-  for (int j = 1; j < 4; ++j) w[j] = (double)iv[j] * 0x1p-58 + dv[j];
+  for (int j = 1; j < 4; ++j) w[j] = (double)iv[j] * 0x1p-58;
   store_warp_sums(w, partials);
 }
 
-// HP_POW2: (1 - w+)/2 is +-2^-k (w+ = 1.25, 1.5, 0.75, ...), so the nine
-// even-part products are shifts.
-template <bool REDUCE, bool HP_POW2>
-__global__ void __launch_bounds__(kSweepThreads, REDUCE ? LBM_FX_RED_MIN_BLOCKS : LBM_FX_MIN_BLOCKS)
-    sweep_fx_kernel(const double* __restrict__ src, double* __restrict__ dst,
-                    const int32_t* __restrict__ adj, int32_t n, FxCoef k, Coef<double> kd,
-                    double* __restrict__ partials) {
-  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
-  double red[4] = {0.0, 0.0, 0.0, 0.0};   // IEEE-path cells: rho, u
-  int64_t ired[4] = {0, 0, 0, 0};         // fixed-point cells: rho - 1, u in units U
-  int nfix = 0;
-  if (i < n) {
-    int32_t idx[18];
+__device__ __forceinline__ void fx_ieee_warp_add(double dv[4], bool ieee, double* partials) {
+  if (!__any_sync(0xffffffffu, ieee)) return;
 #pragma unroll
-    for (int q = 0; q < 18; ++q) idx[q] = __ldg(adj + q * n + i);
-    int64_t b[19];
-    b[0] = __double_as_longlong(__ldg(src + i));
+  for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-    for (int q = 1; q < 19; ++q) b[q] = __double_as_longlong(__ldg(src + idx[q - 1]));
-    bool fast = true;
+    for (int j = 0; j < 4; ++j) dv[j] += __shfl_down_sync(0xffffffffu, dv[j], o);
+  if ((threadIdx.x & 31) == 0) {
+    double* o = partials + 4 * ((int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5));
 #pragma unroll
-    for (int q = 0; q < 19; ++q) fast &= (b[q] >> 52) == wexp(q);
-    int64_t X[19], S[9], D[9], drho = 0, ux = 0, uy = 0, uz = 0;
-    if (fast) {
+    for (int j = 0; j < 4; ++j) o[j] += dv[j];
+  }
+}
+
+// Pulls the raw bits of cell i's 19 PDFs.
+__device__ __forceinline__ void fx_pull(const double* __restrict__ src,
+                                        const int32_t* __restrict__ adj, int32_t n, int32_t i,
+                                        int64_t b[19]) {
+  int32_t idx[18];
 #pragma unroll
-      for (int q = 0; q < 19; ++q) X[q] = (b[q] - wbits(q)) << wshift(q);
+  for (int q = 0; q < 18; ++q) idx[q] = __ldg(adj + q * n + i);
+  b[0] = __double_as_longlong(__ldg(src + i));
 #pragma unroll
-      for (int p = 0; p < 9; ++p) {
-        S[p] = X[2 * p + 1] + X[2 * p + 2];
-        D[p] = X[2 * p + 1] - X[2 * p + 2];
-      }
-      drho = X[0] + (((S[0] + S[1]) + (S[2] + S[3])) + ((S[4] + S[5]) + (S[6] + S[7])) + S[8]);
-      ux = (((D[0] + D[3]) + (D[4] + D[5])) + D[6]) + k.hF[0];
-      uy = (((D[1] + D[3]) - (D[4] - D[7])) + D[8]) + k.hF[1];
-      uz = (((D[2] + D[5]) - (D[6] - D[7])) - D[8]) + k.hF[2];
-      // exact quadratic terms need |u| < 2^-6 (2^52 units)
-      const int64_t lim = 1LL << 52;
-      fast = ux > -lim && ux < lim && uy > -lim && uy < lim && uz > -lim && uz < lim;
-    }
-    if (fast) {
-      const int64_t V1x = fxmul(ux, k.a1) + k.bF1[0];
-      const int64_t V1y = fxmul(uy, k.a1) + k.bF1[1];
-      const int64_t V1z = fxmul(uz, k.a1) + k.bF1[2];
-      const int64_t V2x = V1x >> 1, V2y = V1y >> 1, V2z = V1z >> 1;
-      // Quadratic terms w+ w_p (4.5 (c.u)^2 - 1.5 u.u) = (w+ w_p / 2)
-      // (9 (c.u)^2 - 3 u.u): with v = (w+/36) u, the products
-      // T_ab = v_a u_b carry the class-1 factor (w+ w1 / 2 = w+/36), so
-      // quad_1 = 9 T_aa - 3 T_tr and quad_2 = that expression / 2 for the
-      // diagonal (c.u)^2 = T_aa + T_bb +- 2 T_ab.
-      const int64_t vx = fxmul(ux, k.q1), vy = fxmul(uy, k.q1), vz = fxmul(uz, k.q1);
-      const int64_t Txx = uprod(vx, ux), Tyy = uprod(vy, uy), Tzz = uprod(vz, uz);
-      const int64_t Txy2 = 2 * uprod(vx, uy), Txz2 = 2 * uprod(vx, uz), Tyz2 = 2 * uprod(vy, uz);
-      const int64_t Ttr3 = 3 * (Txx + Tyy + Tzz);
-      const int64_t R1 = fxmul(drho, k.w1p);
-      const int64_t R2 = R1 >> 1;
-      int64_t out[19];
+  for (int q = 1; q < 19; ++q) b[q] = __double_as_longlong(__ldg(src + idx[q - 1]));
+}
+
+// The exact moments of the pulled values: pair sums S, pair differences D,
+// rho - 1 and u, in units U.  False if the cell must take the IEEE path (a
+// PDF outside its binary range, or |u| >= 2^-6).
+__device__ __forceinline__ bool fx_moments(const int64_t b[19], const FxCoef& k, int64_t S[9],
+                                           int64_t D[9], int64_t& drho, int64_t& ux,
+                                           int64_t& uy, int64_t& uz) {
+  bool fast = true;
+#pragma unroll
+  for (int q = 0; q < 19; ++q) fast &= (b[q] >> 52) == wexp(q);
+  if (!fast) return false;
+  int64_t X[19];
+#pragma unroll
+  for (int q = 0; q < 19; ++q) X[q] = (b[q] - wbits(q)) << wshift(q);
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    S[p] = X[2 * p + 1] + X[2 * p + 2];
+    D[p] = X[2 * p + 1] - X[2 * p + 2];
+  }
+  drho = X[0] + (((S[0] + S[1]) + (S[2] + S[3])) + ((S[4] + S[5]) + (S[6] + S[7])) + S[8]);
+  ux = (((D[0] + D[3]) + (D[4] + D[5])) + D[6]) + k.hF[0];
+  uy = (((D[1] + D[3]) - (D[4] - D[7])) + D[8]) + k.hF[1];
+  uz = (((D[2] + D[5]) - (D[6] - D[7])) - D[8]) + k.hF[2];
+  // exact quadratic terms need |u| < 2^-6 (2^52 units)
+  const int64_t lim = 1LL << 52;
+  return ux > -lim && ux < lim && uy > -lim && uy < lim && uz > -lim && uz < lim;
+}
+
+// The fixed-point TRT collision of one cell from its exact moments, and the
+// store of its 19 results.  HP_POW2: (1 - w+)/2 is +-2^-k (w+ = 1.25, 1.5,
+// 0.75, ...), so the nine even-part products are shifts.
+template <bool HP_POW2>
+__device__ __forceinline__ void fx_collide_store(const int64_t S[9], const int64_t D[9],
+                                                 int64_t drho, int64_t ux, int64_t uy,
+                                                 int64_t uz, const FxCoef& k,
+                                                 double* __restrict__ dst, int32_t n, int32_t i) {
+  const int64_t V1x = fxmul(ux, k.a1) + k.bF1[0];
+  const int64_t V1y = fxmul(uy, k.a1) + k.bF1[1];
+  const int64_t V1z = fxmul(uz, k.a1) + k.bF1[2];
+  const int64_t V2x = V1x >> 1, V2y = V1y >> 1, V2z = V1z >> 1;
+  // Quadratic terms w+ w_p (4.5 (c.u)^2 - 1.5 u.u) = (w+ w_p / 2)
+  // (9 (c.u)^2 - 3 u.u): with v = (w+/36) u, the products
+  // T_ab = v_a u_b carry the class-1 factor (w+ w1 / 2 = w+/36), so
+  // quad_1 = 9 T_aa - 3 T_tr and quad_2 = that expression / 2 for the
+  // diagonal (c.u)^2 = T_aa + T_bb +- 2 T_ab.
+  const int64_t vx = fxmul(ux, k.q1), vy = fxmul(uy, k.q1), vz = fxmul(uz, k.q1);
+  const int64_t Txx = uprod(vx, ux), Tyy = uprod(vy, uy), Tzz = uprod(vz, uz);
+  const int64_t Txy2 = 2 * uprod(vx, uy), Txz2 = 2 * uprod(vx, uz), Tyz2 = 2 * uprod(vy, uz);
+  const int64_t Ttr3 = 3 * (Txx + Tyy + Tzz);
+  const int64_t R1 = fxmul(drho, k.w1p);
+  const int64_t R2 = R1 >> 1;
+  int64_t out[19];
 #define LBM_FX_PAIR(P, QUAD, R, VX)                                         \
   {                                                                         \
     const int64_t hS_ = HP_POW2 ? (k.hp_sign > 0 ? S[P] >> k.hp_shift       \
-                                                 : -(S[P] >> k.hp_shift))   \
-                                : fxmul(S[P], k.hp);                        \
+                                             : -(S[P] >> k.hp_shift))   \
+                            : fxmul(S[P], k.hp);                        \
     const int64_t P_ = hS_ + R + (QUAD);                                    \
     const int64_t Q_ = fxmul(D[P], k.hm) + (VX);                            \
     out[2 * P + 1] = P_ + Q_;                                               \
     out[2 * P + 2] = P_ - Q_;                                               \
   }
-      LBM_FX_PAIR(0, 9 * Txx - Ttr3, R1, V1x)
-      LBM_FX_PAIR(1, 9 * Tyy - Ttr3, R1, V1y)
-      LBM_FX_PAIR(2, 9 * Tzz - Ttr3, R1, V1z)
-      LBM_FX_PAIR(3, (9 * (Txx + Tyy + Txy2) - Ttr3) >> 1, R2, V2x + V2y)
-      LBM_FX_PAIR(4, (9 * (Txx + Tyy - Txy2) - Ttr3) >> 1, R2, V2x - V2y)
-      LBM_FX_PAIR(5, (9 * (Txx + Tzz + Txz2) - Ttr3) >> 1, R2, V2x + V2z)
-      LBM_FX_PAIR(6, (9 * (Txx + Tzz - Txz2) - Ttr3) >> 1, R2, V2x - V2z)
-      LBM_FX_PAIR(7, (9 * (Tyy + Tzz + Tyz2) - Ttr3) >> 1, R2, V2y + V2z)
-      LBM_FX_PAIR(8, (9 * (Tyy + Tzz - Tyz2) - Ttr3) >> 1, R2, V2y - V2z)
+  LBM_FX_PAIR(0, 9 * Txx - Ttr3, R1, V1x)
+  LBM_FX_PAIR(1, 9 * Tyy - Ttr3, R1, V1y)
+  LBM_FX_PAIR(2, 9 * Tzz - Ttr3, R1, V1z)
+  LBM_FX_PAIR(3, (9 * (Txx + Tyy + Txy2) - Ttr3) >> 1, R2, V2x + V2y)
+  LBM_FX_PAIR(4, (9 * (Txx + Tyy - Txy2) - Ttr3) >> 1, R2, V2x - V2y)
+  LBM_FX_PAIR(5, (9 * (Txx + Tzz + Txz2) - Ttr3) >> 1, R2, V2x + V2z)
+  LBM_FX_PAIR(6, (9 * (Txx + Tzz - Txz2) - Ttr3) >> 1, R2, V2x - V2z)
+  LBM_FX_PAIR(7, (9 * (Tyy + Tzz + Tyz2) - Ttr3) >> 1, R2, V2y + V2z)
+  LBM_FX_PAIR(8, (9 * (Tyy + Tzz - Tyz2) - Ttr3) >> 1, R2, V2y - V2z)
 #undef LBM_FX_PAIR
-      // Round the moving populations to their storage units (2^-57 axis,
-      // 2^-58 diagonal); the rest population takes the remainder rounded to
-      // its unit 2^-54, and the last -8..7 units go to a diagonal
-      // population, so the stored deviations sum exactly to drho: every
-      // step conserves the stored mass bit for bit.
-      int64_t d[19];
-      int64_t stored = 0;
+  // Round the moving populations to their storage units (2^-57 axis,
+  // 2^-58 diagonal); the rest population takes the remainder rounded to
+  // its unit 2^-54, and the last -8..7 units go to a diagonal
+  // population, so the stored deviations sum exactly to drho: every
+  // step conserves the stored mass bit for bit.
+  int64_t d[19];
+  int64_t stored = 0;
 #pragma unroll
-      for (int q = 1; q < 19; ++q) {
-        const int s = wshift(q);
-        d[q] = s ? (out[q] + (1LL << (s - 1))) >> s : out[q];
-        stored += d[q] << s;
-      }
-      const int64_t rem = drho - stored;
-      d[0] = (rem + 8) >> 4;
-      d[7] += rem - (d[0] << 4);
-      // Store the fixed-point result; an output that left its binary range
-      // (rare) is rewritten through FP64 in a separate branch, so the
-      // common path issues no FP64 instruction at all.
-      uint32_t out_of_range = 0;
+  for (int q = 1; q < 19; ++q) {
+    const int s = wshift(q);
+    d[q] = s ? (out[q] + (1LL << (s - 1))) >> s : out[q];
+    stored += d[q] << s;
+  }
+  const int64_t rem = drho - stored;
+  d[0] = (rem + 8) >> 4;
+  d[7] += rem - (d[0] << 4);
+  // Store the fixed-point result; an output that left its binary range
+  // (rare) is rewritten through FP64 in a separate branch, so the
+  // common path issues no FP64 instruction at all.
+  uint32_t out_of_range = 0;
 #pragma unroll
-      for (int q = 0; q < 19; ++q) {
-        const int64_t bits = wbits(q) + d[q];
-        out_of_range |= (uint32_t)((bits >> 52) != wexp(q)) << q;
-        __stcs(dst + q * n + i, __longlong_as_double(bits));
-      }
-      if (out_of_range) {
-        for (int q = 0; q < 19; ++q)
-          if ((out_of_range >> q) & 1u)
-            dst[q * n + i] = weight(q) + (double)(d[q] << wshift(q)) * 0x1p-58;
-      }
-      if (REDUCE) {
-        ired[0] = drho;
-        ired[1] = ux;
-        ired[2] = uy;
-        ired[3] = uz;
-        nfix = 1;
-      }
+  for (int q = 0; q < 19; ++q) {
+    const int64_t bits = wbits(q) + d[q];
+    out_of_range |= (uint32_t)((bits >> 52) != wexp(q)) << q;
+    __stcs(dst + q * n + i, __longlong_as_double(bits));
+  }
+  if (out_of_range) {
+    for (int q = 0; q < 19; ++q)
+      if ((out_of_range >> q) & 1u)
+        dst[q * n + i] = weight(q) + (double)(d[q] << wshift(q)) * 0x1p-58;
+  }
+}
+
+// The IEEE FP64 collision of one cell (out-of-range cells) and its store.
+__device__ __forceinline__ void fx_ieee_collide_store(double g[19], const Coef<double>& kd,
+                                                      double* __restrict__ dst, int32_t n,
+                                                      int32_t i, double red[4]) {
+  double rho, u[3];
+  collide<double, false>(g, kd, 0.0, rho, u);
+#pragma unroll
+  for (int q = 0; q < 19; ++q) __stcs(dst + q * n + i, g[q]);
+  red[0] = rho;
+  red[1] = u[0];
+  red[2] = u[1];
+  red[3] = u[2];
+}
+
+// A step that does not reduce.
+template <bool HP_POW2>
+__global__ void __launch_bounds__(kSweepThreads, LBM_FX_MIN_BLOCKS)
+    sweep_fx_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                    const int32_t* __restrict__ adj, int32_t n, FxCoef k, Coef<double> kd) {
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  if (i < n) {
+    int64_t b[19];
+    fx_pull(src, adj, n, i, b);
+    int64_t S[9], D[9], drho = 0, ux = 0, uy = 0, uz = 0;
+    if (fx_moments(b, k, S, D, drho, ux, uy, uz)) {
+      fx_collide_store<HP_POW2>(S, D, drho, ux, uy, uz, k, dst, n, i);
     } else {
-      double g[19];
+      double g[19], red[4];
 #pragma unroll
       for (int q = 0; q < 19; ++q) g[q] = __longlong_as_double(b[q]);
-      double rho, u[3];
-      collide<double, false>(g, kd, 0.0, rho, u);
-#pragma unroll
-      for (int q = 0; q < 19; ++q) __stcs(dst + q * n + i, g[q]);
-      if (REDUCE) {
-        red[0] = rho;
-        red[1] = u[0];
-        red[2] = u[1];
-        red[3] = u[2];
-      }
+      fx_ieee_collide_store(g, kd, dst, n, i, red);
     }
   }
-  if (REDUCE) fx_warp_sums(ired, nfix, red, i < n && nfix == 0, partials);
+}
+
+// The reducing step.  The fixed-point moments are summed per warp before the
+// collision, and a cell that takes the IEEE path pulls its values again
+// rather than keep the raw bits live: the reduction then adds little to the
+// registers the collision needs.  (Sharing this structure with the plain
+// step made that one spill.)
+template <bool HP_POW2>
+__global__ void __launch_bounds__(kSweepThreads, LBM_FX_RED_MIN_BLOCKS)
+    sweep_fx_reduce_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                           const int32_t* __restrict__ adj, int32_t n, FxCoef k,
+                           Coef<double> kd, double* __restrict__ partials) {
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  const bool live = i < n;
+  bool fast = false;
+  int64_t S[9], D[9], drho = 0, ux = 0, uy = 0, uz = 0;
+  if (live) {
+    int64_t b[19];
+    fx_pull(src, adj, n, i, b);
+    fast = fx_moments(b, k, S, D, drho, ux, uy, uz);
+  }
+  fast ? fx_fixed_warp_sums(drho, ux, uy, uz, 1, partials)
+       : fx_fixed_warp_sums(0, 0, 0, 0, 0, partials);
+  double red[4] = {0.0, 0.0, 0.0, 0.0};   // IEEE-path cells: rho, u
+  if (live) {
+    if (fast) {
+      fx_collide_store<HP_POW2>(S, D, drho, ux, uy, uz, k, dst, n, i);
+    } else {
+      double g[19];
+      g[0] = __ldg(src + i);
+#pragma unroll
+      for (int q = 1; q < 19; ++q) g[q] = __ldg(src + __ldg(adj + (q - 1) * n + i));
+      fx_ieee_collide_store(g, kd, dst, n, i, red);
+    }
+  }
+  fx_ieee_warp_add(red, live && !fast, partials);
 }
 
 int64_t c63(double c) { return (int64_t)std::llround(c * 0x1p63); }
@@ -266,11 +329,11 @@ int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const 
     double* dst = (double*)st->buf[st->cur ^ 1];
     if (n > 0) {
       if (reduce_last && t == n_steps - 1)
-        pow2 ? sweep_fx_kernel<true, true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials)
-             : sweep_fx_kernel<true, false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials);
+        pow2 ? sweep_fx_reduce_kernel<true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials)
+             : sweep_fx_reduce_kernel<false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials);
       else
-        pow2 ? sweep_fx_kernel<false, true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials)
-             : sweep_fx_kernel<false, false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials);
+        pow2 ? sweep_fx_kernel<true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd)
+             : sweep_fx_kernel<false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd);
     }
     st->cur ^= 1;
   }
