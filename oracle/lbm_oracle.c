@@ -9,8 +9,8 @@
  * method's definition:
  *
  *   - the numbering scheme I(x,y,z) (lexicographic, lexicographic with
- *     blocking, Z curve with 1-bit and 2-bit interleave) applied to all
- *     cells, and the contiguous index I_c = rank of a fluid cell in that
+ *     blocking, Z curve with 1-bit and 2-bit interleave, and the Hilbert
+ *     curve by Skilling's transform) applied to all cells, and the contiguous index I_c = rank of a fluid cell in that
  *     order, solids excluded (Sec. 3, "Numbering scheme" and the definition
  *     of I_c in [1, N_f]);
  *   - the adjacency list of the sparse representation with implicit bounce
@@ -23,7 +23,10 @@
  *     half-way bounce back at solid cells and closed faces, then collides.
  *     It never touches an adjacency list, so an adjacency bug cannot cancel.
  *   - the adjoint (reverse mode) of the time loop through the exact Jacobian
- *     of the collision, for gradients of the mean axial velocity.
+ *     of the collision, for gradients of the mean axial velocity;
+ *   - one step on a given sparse list (pull through an explicit adjacency,
+ *     then the same collision), used to check chunked runs whose lists
+ *     carry ghost slots.
  *
  * The paper names TRT [Ginzburg] but does not print its equations.  The
  * readings used here (see the design notes of the repository):
