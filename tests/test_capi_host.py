@@ -60,3 +60,14 @@ def test_host_side_validation(lib):
     with pytest.raises(capi.LbmError) as ei:
         capi.lbm_build_sparse(0, (4, 4, 4), ordering, 0)
     assert ei.value.status == capi.LBM_EINVAL
+
+
+def test_missing_library_is_an_error_not_a_fallback(monkeypatch, tmp_path):
+    """Without the CUDA library every entry point fails loudly; nothing falls
+    back to another implementation."""
+    monkeypatch.setattr(capi, "_lib", None)
+    monkeypatch.setattr(capi, "library_path", lambda: str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="is missing"):
+        capi.load()
+    with pytest.raises(RuntimeError, match="is missing"):
+        capi.lbm_abi_version()
