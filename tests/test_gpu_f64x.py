@@ -75,8 +75,15 @@ def test_out_of_range_cells_fall_back_to_fp64(shape, periodic):
     st = LBMState(lat, "f64x")
     st.set_pdfs(torch.from_numpy(oracle.to_sparse(f0, cells).copy()))
     st.step(5, WP, WM, F)
-    f_ref, _, _, _ = oracle.run(flags, periodic, WP, WM, F, 5, f=f0)
+    f_ref, obs, _, _ = oracle.run(flags, periodic, WP, WM, F, 5, f=f0)
     assert _rel(st.get_pdfs().cpu().numpy(), oracle.to_sparse(f_ref, cells)) < 1e-12
+    # the reduction adds the IEEE-path cells' FP64 moments to the warp slots
+    # that the fixed-point cells wrote
+    n = lat.n
+    for axis in range(3):
+        mass, flux = st.reduce_flux(axis)
+        assert abs(mass - obs[-1, 0]) <= 1e-12 * abs(obs[-1, 0])
+        assert abs(flux - obs[-1, 1 + axis] / n) <= 1e-12 * max(1.0, abs(obs[-1, 1:]).max() / n)
     st.close()
     lat.close()
 
