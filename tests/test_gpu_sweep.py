@@ -72,6 +72,33 @@ def test_tiny_boxes_random_state_parity(shape, periodic):
         lat.close()
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32s"])
+def test_reduction_of_large_moments_takes_the_fp64_path(precision):
+    """States far from rest (|rho - 1| and |u| up to ~1): warps holding a
+    value >= 1/4 sum in FP64 instead of fixed point, mixed with warps that
+    do not; mass and flux must still match the oracle."""
+    rng = np.random.default_rng(11)
+    shape = (12, 10, 9)
+    flags = (rng.random(shape) < 0.2).astype(np.uint8)
+    f0 = oracle.rest_state(flags) * (1 + 0.02 * rng.standard_normal((19,) + shape))
+    hot = rng.random(shape) < 0.1           # a tenth of the cells far from rest
+    f0[:, hot] *= 1 + 0.9 * rng.random((19, int(hot.sum())))
+    F = (1e-3, -2e-3, 3e-3)
+    lat, st, cells = _gpu_run(flags, 0b111, 1, F, precision=precision, f0_dense=f0)
+    _, obs, rho_ref, u_ref = oracle.run(flags, 0b111, WP, WM, F, 1, f=f0)
+    rho_s = oracle.to_sparse(rho_ref, cells)
+    assert np.abs(rho_s - 1).max() >= 0.25     # the FP64 path is taken
+    tol = 1e-13 if precision == "f64" else 1e-6
+    mass, _ = st.reduce_flux(0)
+    assert abs(mass - obs[-1, 0]) <= tol * abs(obs[-1, 0])
+    for axis in range(3):
+        _, flux = st.reduce_flux(axis)
+        ref = obs[-1, 1 + axis] / lat.n
+        assert abs(flux - ref) <= tol * np.abs(u_ref).max(), (axis, flux, ref)
+    st.close()
+    lat.close()
+
+
 def test_small_bed_1000_steps_parity():
     """The 32x32x64 packed bed, lexicographic order, 1000 FP64 steps from
     rest with F = 1e-6 along z."""
