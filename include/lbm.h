@@ -185,6 +185,17 @@ int lbm_step(lbm_state* st, int32_t n_steps, double omega_plus, double omega_min
              const double force[3]);
 
 /*
+ * lbm_step, timed on the device: CUDA events recorded on the state's stream
+ * just before and after the step launches give the device time of the
+ * n_steps steps (the reducing last one included) in *ms_out, in
+ * milliseconds.  Synchronises the stream (bounded by lbm_set_timeout).  The
+ * events are created on the first call and kept until lbm_free.  Errors:
+ * those of lbm_step, LBM_EINVAL (ms_out NULL), LBM_ETIMEOUT, LBM_ECUDA.
+ */
+int lbm_step_timed(lbm_state* st, int32_t n_steps, double omega_plus, double omega_minus,
+                   const double force[3], double* ms_out);
+
+/*
  * Mass and mean axial velocity of the most recent step's collision:
  * mass = sum_n rho_n and flux = (1/N) sum_n u_axis,n, returned in FP64.
  * Within each warp of 32 cells, rho - 1 and u are summed exactly as int64

@@ -40,6 +40,7 @@ SIGNATURES = {
     "lbm_state_reset": (ctypes.c_int, [_vp]),
     "lbm_set_damping": (ctypes.c_int, [_vp, _vp]),
     "lbm_step": (ctypes.c_int, [_vp, _i32, _d, _d, _vp]),
+    "lbm_step_timed": (ctypes.c_int, [_vp, _i32, _d, _d, _vp, _vp]),
     "lbm_reduce_flux": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
     "lbm_moments": (ctypes.c_int, [_vp, _vp, _vp]),
     "lbm_state_steps": (ctypes.c_int, [_vp, _vp]),
@@ -150,6 +151,16 @@ def lbm_set_damping(state: int, alpha_dev) -> None:
 def lbm_step(state: int, n_steps: int, omega_plus: float, omega_minus: float, force) -> None:
     f = (ctypes.c_double * 3)(*[float(v) for v in force])
     _check(load().lbm_step(state, int(n_steps), float(omega_plus), float(omega_minus), f))
+
+
+def lbm_step_timed(state: int, n_steps: int, omega_plus: float, omega_minus: float,
+                   force) -> float:
+    """lbm_step, returning the device time of the steps in milliseconds."""
+    f = (ctypes.c_double * 3)(*[float(v) for v in force])
+    ms = ctypes.c_double(0.0)
+    _check(load().lbm_step_timed(state, int(n_steps), float(omega_plus), float(omega_minus), f,
+                                 ctypes.byref(ms)))
+    return ms.value
 
 
 def lbm_reduce_flux(state: int, axis: int):

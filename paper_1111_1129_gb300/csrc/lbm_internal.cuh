@@ -288,6 +288,7 @@ struct lbm_state {
   double last_force[3];
   double last_wp, last_wm;
   cudaEvent_t done;    // recorded to wait for the stream with a time limit
+  cudaEvent_t t0, t1;  // timing events of lbm_step_timed (created on first use)
   lbm::StepGraph* graph;  // cached CUDA graphs of non-reducing steps, or null
   lbm::Batch* batch;   // non-null for a batched state (sp is then owned)
 };

@@ -284,6 +284,8 @@ void free_state(lbm_state* st) {
     if (p) cudaFree(p);
   if (st->red_host) cudaFreeHost(st->red_host);
   if (st->done) cudaEventDestroy(st->done);
+  if (st->t0) cudaEventDestroy(st->t0);
+  if (st->t1) cudaEventDestroy(st->t1);
   free_graph(st);
   if (st->batch) free_batch(st);
   st->magic = 0;
@@ -411,6 +413,32 @@ extern "C" int lbm_step(lbm_state* st, int32_t n_steps, double omega_plus, doubl
   st->last_wp = omega_plus;
   st->last_wm = omega_minus;
   for (int d = 0; d < 3; ++d) st->last_force[d] = force[d];
+  return LBM_OK;
+}
+
+extern "C" int lbm_step_timed(lbm_state* st, int32_t n_steps, double omega_plus,
+                              double omega_minus, const double force[3], double* ms_out) {
+  clear_error();
+  if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  if (!ms_out) return fail(LBM_EINVAL, "ms_out is NULL");
+  if (!st->t0) {
+    if (cudaEventCreate(&st->t0) != cudaSuccess || cudaEventCreate(&st->t1) != cudaSuccess) {
+      cudaGetLastError();
+      if (st->t0) cudaEventDestroy(st->t0);
+      st->t0 = st->t1 = nullptr;
+      return fail(LBM_ECUDA, "cudaEventCreate failed");
+    }
+  }
+  const cudaStream_t stream = st->sp->stream;
+  LBM_CUDA_TRY(cudaEventRecord(st->t0, stream));
+  int rc = lbm_step(st, n_steps, omega_plus, omega_minus, force);
+  if (rc != LBM_OK) return rc;
+  LBM_CUDA_TRY(cudaEventRecord(st->t1, stream));
+  rc = wait_event(st->done, stream, 0.0);
+  if (rc != LBM_OK) return rc;
+  float ms = 0.f;
+  LBM_CUDA_TRY(cudaEventElapsedTime(&ms, st->t0, st->t1));
+  *ms_out = (double)ms;
   return LBM_OK;
 }
 

@@ -162,6 +162,11 @@ class LBMState:
     def step(self, n_steps: int, omega_plus: float, omega_minus: float, force) -> None:
         capi.lbm_step(self._handle, n_steps, omega_plus, omega_minus, force)
 
+    def step_timed(self, n_steps: int, omega_plus: float, omega_minus: float, force) -> float:
+        """``step``, returning the device time of the steps in milliseconds
+        (CUDA events on the state's stream; synchronises)."""
+        return capi.lbm_step_timed(self._handle, n_steps, omega_plus, omega_minus, force)
+
     def reduce_flux(self, axis: int):
         """(mass, mean axial velocity) of the most recent step, FP64."""
         return capi.lbm_reduce_flux(self._handle, axis)
