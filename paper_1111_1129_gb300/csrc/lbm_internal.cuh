@@ -269,6 +269,32 @@ struct StepGraph {
   double wp[2], wm[2], F[2][3];
   const void* alpha[2];
 };
+
+// Launches a sweep on `stream` in blocks of kSweepThreads.  `chained` means
+// the previous launch on the stream is a sweep of the same lbm_step call: the
+// launch then allows programmatic stream serialisation, so its blocks can
+// start (and load their adjacency entries) while that sweep finishes.  The
+// sweep kernels order every other access behind prior_step_done().  Build
+// with -DLBM_CHAIN_STEPS=0 to launch every sweep normally.
+#ifndef LBM_CHAIN_STEPS
+#define LBM_CHAIN_STEPS 1
+#endif
+template <class... P, class... A>
+cudaError_t launch_sweep(void (*kernel)(P...), unsigned grid, cudaStream_t stream, bool chained,
+                         A... args) {
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kSweepThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  const bool pdl = LBM_CHAIN_STEPS && chained;
+  cfg.attrs = pdl ? &attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 }  // namespace lbm
 
 struct lbm_state {
@@ -282,6 +308,7 @@ struct lbm_state {
   double* partials;    // [nblocks * kWarpsPerBlock * 4] FP64 warp sums of the last step,
                        // then [nblocks * 4] block values formed by lbm_reduce_flux
   int64_t nblocks;
+  bool one_wave;       // nblocks <= 4 x SMs: plain FP32/16-bit steps load links first
   double* red_dev;     // [4] final sums
   double* red_host;    // [4] pinned
   int64_t steps;

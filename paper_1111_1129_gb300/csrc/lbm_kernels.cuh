@@ -106,25 +106,59 @@ __device__ __forceinline__ typename Form<PREC>::S encode(typename Form<PREC>::C 
   else return v;
 }
 
+// Global loads through the non-coherent path and streaming (evict-first)
+// stores, as volatile inline PTX.  The compiler keeps volatile asm in program
+// order, so in a chained step (prior_step_done() below) no PDF is read or
+// written before the wait.
+__device__ __forceinline__ double ld_nc(const double* p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_nc(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int32_t ld_nc(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned short ld_nc(const unsigned short* p) {
+  unsigned short v;
+  asm volatile("ld.global.nc.u16 %0, [%1];" : "=h"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void st_cs(double* p, double v) {
+  asm volatile("st.global.cs.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_cs(float* p, float v) {
+  asm volatile("st.global.cs.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_cs(unsigned short* p, unsigned short v) {
+  asm volatile("st.global.cs.u16 [%0], %1;" ::"l"(p), "h"(v) : "memory");
+}
+
 template <int PREC>
 __device__ __forceinline__ typename Form<PREC>::S load_ro(const typename Form<PREC>::S* p) {
   if constexpr (PREC == LBM_F16S) {
-    return __ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p)));
+    return __ushort_as_half(ld_nc(reinterpret_cast<const unsigned short*>(p)));
   } else if constexpr (PREC == LBM_BF16S) {
-    return __ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p)));
+    return __ushort_as_bfloat16(ld_nc(reinterpret_cast<const unsigned short*>(p)));
   } else {
-    return __ldg(p);
+    return ld_nc(p);
   }
 }
 
 template <int PREC>
 __device__ __forceinline__ void store_stream(typename Form<PREC>::S* p, typename Form<PREC>::S v) {
   if constexpr (PREC == LBM_F16S) {
-    __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(v));
+    st_cs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(v));
   } else if constexpr (PREC == LBM_BF16S) {
-    __stcs(reinterpret_cast<unsigned short*>(p), __bfloat16_as_ushort(v));
+    st_cs(reinterpret_cast<unsigned short*>(p), __bfloat16_as_ushort(v));
   } else {
-    __stcs(p, v);
+    st_cs(p, v);
   }
 }
 
@@ -286,6 +320,24 @@ __device__ __forceinline__ void store_block_sums(const double w[4], double* out)
   }
 }
 
+// The 18 adjacency entries of cell i (the source slot of each pulled q > 0).
+__device__ __forceinline__ void load_links(const int32_t* __restrict__ adj, int32_t n, int32_t i,
+                                           int32_t idx[18]) {
+#pragma unroll
+  for (int q = 0; q < 18; ++q) idx[q] = ld_nc(adj + q * n + i);
+}
+
+// The 19 pulled values of cell i, given its adjacency entries.
+template <int PREC>
+__device__ __forceinline__ void pull(const typename Form<PREC>::S* __restrict__ src,
+                                     const int32_t idx[18], int32_t i,
+                                     typename Form<PREC>::C inv_scale,
+                                     typename Form<PREC>::C g[19]) {
+  g[0] = decode<PREC>(load_ro<PREC>(src + i), inv_scale);
+#pragma unroll
+  for (int q = 1; q < 19; ++q) g[q] = decode<PREC>(load_ro<PREC>(src + idx[q - 1]), inv_scale);
+}
+
 // Gathers the 19 pulled values of cell i.
 template <int PREC>
 __device__ __forceinline__ void gather(const typename Form<PREC>::S* __restrict__ src,
@@ -293,24 +345,42 @@ __device__ __forceinline__ void gather(const typename Form<PREC>::S* __restrict_
                                        typename Form<PREC>::C inv_scale,
                                        typename Form<PREC>::C g[19]) {
   int32_t idx[18];
-#pragma unroll
-  for (int q = 0; q < 18; ++q) idx[q] = __ldg(adj + q * n + i);
-  g[0] = decode<PREC>(load_ro<PREC>(src + i), inv_scale);
-#pragma unroll
-  for (int q = 1; q < 19; ++q) g[q] = decode<PREC>(load_ro<PREC>(src + idx[q - 1]), inv_scale);
+  load_links(adj, n, i, idx);
+  pull<PREC>(src, idx, i, inv_scale, g);
+}
+
+// ---- chained steps (programmatic dependent launch) --------------------------
+// The second and later sweeps of an lbm_step call are launched with
+// programmatic stream serialisation, so their blocks may start while the
+// previous sweep still runs.  A sweep first loads its adjacency entries,
+// which no step writes.  prior_step_done() then waits until the previous grid
+// has completed and its writes are visible, and lets the next sweep's blocks
+// launch.  PDF and damping accesses are volatile asm (ld_nc, st_cs), which the
+// compiler keeps behind the wait.  The warp sums are plain C++ accesses: the
+// wait returns zero, which the compiler cannot know, and the sums pointer is
+// offset by it.  In a normal launch the wait returns at once.
+__device__ __forceinline__ int32_t prior_step_done() {
+  int32_t zero;
+  asm volatile(
+      "griddepcontrol.wait;\n\t"
+      "griddepcontrol.launch_dependents;\n\t"
+      "mov.b32 %0, 0;"
+      : "=r"(zero)::"memory");
+  return zero;
 }
 
 #ifndef LBM_SWEEP_MIN_BLOCKS
-#define LBM_SWEEP_MIN_BLOCKS 1
+#define LBM_SWEEP_MIN_BLOCKS 4
 #endif
 // Resident 256-thread blocks per SM that the register budget of the FP32 and
-// 16-bit sweeps is sized for (the FP64 sweep is bound by its arithmetic).
-// With 1 the compiler keeps all 18 indices and 19 pulled values of a cell in
-// flight (64 registers, 4 blocks per SM); on the 1024x256x256 bed forcing 5,
-// 6, 7 or 8 blocks per SM cut the FP16 sweep by 3%, 4%, 8% and 8%.
+// 16-bit sweeps is sized for (the FP64-arithmetic sweeps are bound by their
+// arithmetic).  4 holds them at 64 registers, with all 18 indices and 19
+// pulled values of a cell in flight and no spills; left free, the compiler
+// takes 66-78 registers (3 blocks per SM).  On the 1024x256x256 bed forcing
+// 5, 6, 7 or 8 blocks per SM cut the FP16 sweep by 3%, 4%, 8% and 8%.
 template <int PREC>
 constexpr int sweep_min_blocks() {
-  return PREC == LBM_F64 ? 1 : LBM_SWEEP_MIN_BLOCKS;
+  return PREC == LBM_F64 || PREC == LBM_F64X ? 1 : LBM_SWEEP_MIN_BLOCKS;
 }
 
 // RED: 0 no reduction; 1 warp sums into per-warp slots (no block barrier);
@@ -331,7 +401,12 @@ constexpr int sweep_launch_min_blocks() {
                                                                  : sweep_min_blocks<PREC>();
 }
 
-template <int PREC, bool DAMPED, int RED>
+// LINKS_FIRST: load the adjacency entries before waiting for the previous
+// step (a chained launch then overlaps them with that step's end), instead of
+// after.  On a grid of one wave (the 32x32x64 bed) that made the FP32 and
+// 16-bit steps 15-17% faster; on the 1024x256x256 bed it cost the FP16 step
+// 0.9%, and the fixed-point kernel spilled with it.
+template <int PREC, bool DAMPED, int RED, bool LINKS_FIRST = false>
 __global__ void __launch_bounds__(kSweepThreads, sweep_launch_min_blocks<PREC, RED>())
     sweep_kernel(const typename Form<PREC>::S* __restrict__ src,
                  typename Form<PREC>::S* __restrict__ dst, const int32_t* __restrict__ adj,
@@ -340,18 +415,23 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_launch_min_blocks<PREC, R
   using C = typename Form<PREC>::C;
   const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
   C rho = C(0), u[3] = {C(0), C(0), C(0)};
+  int32_t idx[18];
+  int32_t z = 0;
+  if constexpr (!LINKS_FIRST) z = prior_step_done();
+  if (i < n) load_links(adj, n, i, idx);
+  if constexpr (LINKS_FIRST) z = prior_step_done();
   if (i < n) {
     C g[19];
-    gather<PREC>(src, adj, n, i, k.inv_scale, g);
-    collide<C, DAMPED>(g, k, DAMPED ? alpha[i] : C(0), rho, u);
+    pull<PREC>(src, idx, i, k.inv_scale, g);
+    collide<C, DAMPED>(g, k, DAMPED ? ld_nc(alpha + i) : C(0), rho, u);
 #pragma unroll
     for (int q = 0; q < 19; ++q) store_stream<PREC>(dst + q * n + i, encode<PREC>(g[q], k.scale));
   }
   if constexpr (RED != kNoReduce) {
     double w[4];
     warp_flux_sums<C, Form<PREC>::kShifted>(i < n, rho, u, w);
-    if constexpr (RED == kWarpSums) store_warp_sums(w, partials);
-    else store_block_sums(w, partials + 4 * (int64_t)blockIdx.x);
+    if constexpr (RED == kWarpSums) store_warp_sums(w, partials + z);
+    else store_block_sums(w, partials + z + 4 * (int64_t)blockIdx.x);
   }
 }
 

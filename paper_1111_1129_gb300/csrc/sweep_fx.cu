@@ -110,16 +110,12 @@ __device__ __forceinline__ void fx_ieee_warp_add(double dv[4], bool ieee, double
   }
 }
 
-// Pulls the raw bits of cell i's 19 PDFs.
-__device__ __forceinline__ void fx_pull(const double* __restrict__ src,
-                                        const int32_t* __restrict__ adj, int32_t n, int32_t i,
-                                        int64_t b[19]) {
-  int32_t idx[18];
+// Pulls the raw bits of cell i's 19 PDFs, given its adjacency entries.
+__device__ __forceinline__ void fx_pull(const double* __restrict__ src, const int32_t idx[18],
+                                        int32_t i, int64_t b[19]) {
+  b[0] = __double_as_longlong(ld_nc(src + i));
 #pragma unroll
-  for (int q = 0; q < 18; ++q) idx[q] = __ldg(adj + q * n + i);
-  b[0] = __double_as_longlong(__ldg(src + i));
-#pragma unroll
-  for (int q = 1; q < 19; ++q) b[q] = __double_as_longlong(__ldg(src + idx[q - 1]));
+  for (int q = 1; q < 19; ++q) b[q] = __double_as_longlong(ld_nc(src + idx[q - 1]));
 }
 
 // The exact moments of the pulled values: pair sums S, pair differences D,
@@ -217,7 +213,7 @@ __device__ __forceinline__ void fx_collide_store(const int64_t S[9], const int64
   for (int q = 0; q < 19; ++q) {
     const int64_t bits = wbits(q) + d[q];
     out_of_range |= (uint32_t)((bits >> 52) != wexp(q)) << q;
-    __stcs(dst + q * n + i, __longlong_as_double(bits));
+    st_cs(dst + q * n + i, __longlong_as_double(bits));
   }
   if (out_of_range) {
     for (int q = 0; q < 19; ++q)
@@ -233,7 +229,7 @@ __device__ __forceinline__ void fx_ieee_collide_store(double g[19], const Coef<d
   double rho, u[3];
   collide<double, false>(g, kd, 0.0, rho, u);
 #pragma unroll
-  for (int q = 0; q < 19; ++q) __stcs(dst + q * n + i, g[q]);
+  for (int q = 0; q < 19; ++q) st_cs(dst + q * n + i, g[q]);
   red[0] = rho;
   red[1] = u[0];
   red[2] = u[1];
@@ -246,9 +242,12 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_FX_MIN_BLOCKS)
     sweep_fx_kernel(const double* __restrict__ src, double* __restrict__ dst,
                     const int32_t* __restrict__ adj, int32_t n, FxCoef k, Coef<double> kd) {
   const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  prior_step_done();  // a chained launch waits here for the previous step
   if (i < n) {
+    int32_t idx[18];
     int64_t b[19];
-    fx_pull(src, adj, n, i, b);
+    load_links(adj, n, i, idx);
+    fx_pull(src, idx, i, b);
     int64_t S[9], D[9], drho = 0, ux = 0, uy = 0, uz = 0;
     if (fx_moments(b, k, S, D, drho, ux, uy, uz)) {
       fx_collide_store<HP_POW2>(S, D, drho, ux, uy, uz, k, dst, n, i);
@@ -275,26 +274,29 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_FX_RED_MIN_BLOCKS)
   const bool live = i < n;
   bool fast = false;
   int64_t S[9], D[9], drho = 0, ux = 0, uy = 0, uz = 0;
+  const int32_t z = prior_step_done();  // zero, after the previous step has finished
   if (live) {
+    int32_t idx[18];
     int64_t b[19];
-    fx_pull(src, adj, n, i, b);
+    load_links(adj, n, i, idx);
+    fx_pull(src, idx, i, b);
     fast = fx_moments(b, k, S, D, drho, ux, uy, uz);
   }
-  fast ? fx_fixed_warp_sums(drho, ux, uy, uz, 1, partials)
-       : fx_fixed_warp_sums(0, 0, 0, 0, 0, partials);
+  fast ? fx_fixed_warp_sums(drho, ux, uy, uz, 1, partials + z)
+       : fx_fixed_warp_sums(0, 0, 0, 0, 0, partials + z);
   double red[4] = {0.0, 0.0, 0.0, 0.0};   // IEEE-path cells: rho, u
   if (live) {
     if (fast) {
       fx_collide_store<HP_POW2>(S, D, drho, ux, uy, uz, k, dst, n, i);
     } else {
       double g[19];
-      g[0] = __ldg(src + i);
+      g[0] = ld_nc(src + i);
 #pragma unroll
-      for (int q = 1; q < 19; ++q) g[q] = __ldg(src + __ldg(adj + (q - 1) * n + i));
+      for (int q = 1; q < 19; ++q) g[q] = ld_nc(src + __ldg(adj + (q - 1) * n + i));
       fx_ieee_collide_store(g, kd, dst, n, i, red);
     }
   }
-  fx_ieee_warp_add(red, live && !fast, partials);
+  fx_ieee_warp_add(red, live && !fast, partials + z);
 }
 
 int64_t c63(double c) { return (int64_t)std::llround(c * 0x1p63); }
@@ -328,16 +330,17 @@ int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const 
     const double* src = (const double*)st->buf[st->cur];
     double* dst = (double*)st->buf[st->cur ^ 1];
     if (n > 0) {
+      const int32_t* adj = st->sp->adj;
+      const bool chained = t > 0;
       if (reduce_last && t == n_steps - 1)
-        pow2 ? sweep_fx_reduce_kernel<true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials)
-             : sweep_fx_reduce_kernel<false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd, st->partials);
+        LBM_CUDA_TRY(pow2 ? launch_sweep(sweep_fx_reduce_kernel<true>, grid, stream, chained, src, dst, adj, n, k, kd, st->partials)
+                          : launch_sweep(sweep_fx_reduce_kernel<false>, grid, stream, chained, src, dst, adj, n, k, kd, st->partials));
       else
-        pow2 ? sweep_fx_kernel<true><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd)
-             : sweep_fx_kernel<false><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, kd);
+        LBM_CUDA_TRY(pow2 ? launch_sweep(sweep_fx_kernel<true>, grid, stream, chained, src, dst, adj, n, k, kd)
+                          : launch_sweep(sweep_fx_kernel<false>, grid, stream, chained, src, dst, adj, n, k, kd));
     }
     st->cur ^= 1;
   }
-  LBM_CUDA_TRY(cudaGetLastError());
   return LBM_OK;
 }
 
