@@ -139,7 +139,10 @@ __global__ void __launch_bounds__(kSweepThreads)
                         typename Form<PREC>::C* __restrict__ lam_out, double* __restrict__ part,
                         double* __restrict__ dalpha) {
   using C = typename Form<PREC>::C;
-  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  // A chained launch waits for the previous kernel here.  The zero it returns
+  // offsets every index and pointer, so no access can be scheduled earlier.
+  const int32_t z = prior_step_done();
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x + z;
   double red[4] = {0.0, 0.0, 0.0, 0.0};
   if (i < n) {
     C g[19];
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(kSweepThreads)
     red[3] = (double)u[axis];
     dalpha[i] = -0.5 * (double)seed * (double)u[axis];
   }
-  block_accumulate4(red, part + 4 * (int64_t)blockIdx.x, true);
+  block_accumulate4(red, part + z + 4 * (int64_t)blockIdx.x, true);
 }
 
 // One reverse step t: lam_f_t = S^T lam_g_{t+1} (gathered), then
@@ -169,7 +172,8 @@ __global__ void __launch_bounds__(kSweepThreads)
                         typename Form<PREC>::C* __restrict__ lam_out, double* __restrict__ part,
                         double* __restrict__ dalpha) {
   using C = typename Form<PREC>::C;
-  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  const int32_t z = prior_step_done();  // as in adjoint_seed_kernel
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x + z;
   C red[4] = {C(0), C(0), C(0), C(0)};
   if (i < n) {
     int32_t idx[18];
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(kSweepThreads)
     const C M1u = M1x * u[0] + M1y * u[1] + M1z * u[2];
     dalpha[i] += (double)(-hs * Gu - three_src * M1u);
   }
-  block_accumulate4(red, part + 4 * (int64_t)blockIdx.x, false);
+  block_accumulate4(red, part + z + 4 * (int64_t)blockIdx.x, false);
 }
 
 // lam_f_0 = S^T lam_g_1 (gradient with respect to the initial PDFs).
@@ -267,6 +271,12 @@ struct Runner {
   AdjCoef<C> a;
   const C* alpha;
   size_t state_elems;
+  // Kernels after the first of a forward or backward pass are chained
+  // (programmatic dependent launch; the kernels wait for their predecessor),
+  // except in FP64 arithmetic, which chaining slows down.
+  static constexpr bool kChain = PREC != LBM_F64 && PREC != LBM_F64X;
+  mutable bool chained = false;
+  mutable cudaError_t err = cudaSuccess;
 
   Runner(lbm_adjoint* ad_) : ad(ad_), st(ad_->st) {
     n = (int32_t)st->sp->n;
@@ -281,23 +291,23 @@ struct Runner {
   S* seg(int i) const { return (S*)ad->seg + (size_t)i * state_elems; }
   C* lam(int i) const { return (C*)ad->lam[i]; }
 
+  template <class... P, class... A>
+  void launch(void (*kernel)(P...), A... args) const {
+    const cudaError_t e = launch_sweep(kernel, grid, stream, kChain && chained, args...);
+    if (err == cudaSuccess) err = e;
+    chained = true;
+  }
   void step(const S* src, S* dst) const {
-    if (alpha)
-      sweep_kernel<PREC, true, kNoReduce><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, nullptr);
-    else
-      sweep_kernel<PREC, false, kNoReduce><<<grid, kSweepThreads, 0, stream>>>(src, dst, st->sp->adj, n, k, alpha, nullptr);
+    if (alpha) launch(sweep_kernel<PREC, true, kNoReduce>, src, dst, st->sp->adj, n, k, alpha, (double*)nullptr);
+    else launch(sweep_kernel<PREC, false, kNoReduce>, src, dst, st->sp->adj, n, k, alpha, (double*)nullptr);
   }
   void seed(const S* f_prev) const {
-    if (alpha)
-      adjoint_seed_kernel<PREC, true><<<grid, kSweepThreads, 0, stream>>>(f_prev, st->sp->adj, n, k, a, alpha, ad->axis, lam(0), ad->part, ad->dalpha);
-    else
-      adjoint_seed_kernel<PREC, false><<<grid, kSweepThreads, 0, stream>>>(f_prev, st->sp->adj, n, k, a, alpha, ad->axis, lam(0), ad->part, ad->dalpha);
+    if (alpha) launch(adjoint_seed_kernel<PREC, true>, f_prev, st->sp->adj, n, k, a, alpha, ad->axis, lam(0), ad->part, ad->dalpha);
+    else launch(adjoint_seed_kernel<PREC, false>, f_prev, st->sp->adj, n, k, a, alpha, ad->axis, lam(0), ad->part, ad->dalpha);
   }
   void reverse(const S* f_prev, int in) const {
-    if (alpha)
-      adjoint_step_kernel<PREC, true><<<grid, kSweepThreads, 0, stream>>>(f_prev, st->sp->adj, n, k, a, alpha, lam(in), lam(in ^ 1), ad->part, ad->dalpha);
-    else
-      adjoint_step_kernel<PREC, false><<<grid, kSweepThreads, 0, stream>>>(f_prev, st->sp->adj, n, k, a, alpha, lam(in), lam(in ^ 1), ad->part, ad->dalpha);
+    if (alpha) launch(adjoint_step_kernel<PREC, true>, f_prev, st->sp->adj, n, k, a, alpha, lam(in), lam(in ^ 1), ad->part, ad->dalpha);
+    else launch(adjoint_step_kernel<PREC, false>, f_prev, st->sp->adj, n, k, a, alpha, lam(in), lam(in ^ 1), ad->part, ad->dalpha);
   }
 
   // Forward pass from the state's current PDFs: checkpoints f_{j*stride};
@@ -305,6 +315,7 @@ struct Runner {
   int forward(const S** last) const {
     LBM_CUDA_TRY(cudaMemcpyAsync(ckpt(0), st->buf[st->cur], state_elems * sizeof(S),
                                  cudaMemcpyDeviceToDevice, stream));
+    chained = false;
     const S* cur = ckpt(0);
     for (int32_t t = 1; t <= ad->K - 1; ++t) {
       S* dst = (t % ad->stride == 0) ? ckpt(t / ad->stride) : seg(t & 1);
@@ -329,6 +340,7 @@ struct Runner {
   int backward(double* dJdf0) const {
     const int K = ad->K, s = ad->stride;
     int j = (K - 1) / s;
+    chained = false;
     recompute(j, (K - 1) - j * s);
     seed(state_at(j, (K - 1) - j * s));
     int in = 0;
@@ -343,6 +355,7 @@ struct Runner {
     }
     if (dJdf0)
       adjoint_initial_kernel<C><<<grid, kSweepThreads, 0, stream>>>(st->sp->adj, n, lam(in), dJdf0);
+    LBM_CUDA_TRY(err);
     LBM_CUDA_TRY(cudaGetLastError());
     return LBM_OK;
   }
@@ -356,6 +369,7 @@ int run_forward(lbm_adjoint* ad) {
   const int rc = r.forward(&last);
   if (rc != LBM_OK) return rc;
   r.seed(last);
+  LBM_CUDA_TRY(r.err);
   LBM_CUDA_TRY(cudaGetLastError());
   return LBM_OK;
 }
