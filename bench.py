@@ -510,8 +510,9 @@ def run_adjoint_study(args):
 def run_batch_study(args):
     """256 packed beds (cube sides uniform in {24..96}, sphere radii in
     [3, 8], forces in [1e-7, 1e-5] along z), FP32 shifted storage: the
-    autotuned batched launch under a CUDA graph against the same beds
-    stepped one by one; per-bed fluxes are compared bit for bit."""
+    autotuned batched launch in L2 groups, and as one group under a CUDA
+    graph, against the same beds stepped one by one; per-bed fluxes are
+    compared bit for bit."""
     import torch
 
     from paper_1111_1129_gb300 import (BatchedState, LBMState, SparseLattice, capi, inputs,
@@ -539,16 +540,21 @@ def run_batch_study(args):
         return e0.elapsed_time(e1)
 
     out = {}
-    for label, graph in (("batched_graph", True), ("batched_no_graph", False)):
+    for label, graph, group_bytes in (("batched_l2_groups", True, -1),
+                                      ("batched_graph", True, 0),
+                                      ("batched_no_graph", False, 0)):
         bs = BatchedState(lats, "f32s")
         bs.configure(block, cpt, graph)
+        n_groups = bs.groups(group_bytes)
         bs.step(K, WP, wm, forces)          # warm-up; captures the graph
         bs.reset()                          # back to rest, same grid parity
         ms = timed(lambda: bs.step(K, WP, wm, forces))
         mass, flux = bs.reduce_flux(2)
-        out[label] = {"mflups": n_fluid * K / (ms * 1e-3) / 1e6, "ms": ms}
-        if graph:
+        out[label] = {"mflups": n_fluid * K / (ms * 1e-3) / 1e6, "ms": ms, "groups": n_groups}
+        if label == "batched_l2_groups":
             batched_flux = flux
+        else:
+            assert list(flux) == list(batched_flux), "grouping changed a bed's flux"
         bs.close()
     states = [LBMState(l, "f32s") for l in lats]
 
@@ -566,7 +572,7 @@ def run_batch_study(args):
     line = {"study": "batched beds", "n_beds": 256, "fluid_cells": n_fluid, "steps": K,
             "ordering": args.ordering, "precision": "f32s", "tuned": {"block": block, "cells_per_thread": cpt,
                                            "candidate_ms_block_major": cand},
-            **out, "speedup_vs_separate": out["batched_graph"]["mflups"] /
+            **out, "speedup_vs_separate": out["batched_l2_groups"]["mflups"] /
             out["separate_loops"]["mflups"],
             "per_bed_flux_bit_identical": f"{same}/256"}
     print(json.dumps(line), flush=True)

@@ -273,10 +273,11 @@ int lbm_step_f64_noalloc(const double* f_src_dev, double* f_dst_dev, const int32
  *   padded length N_pad; see lbm_batch_layout.  Damping, moments and the
  *   adjoint are not available on a batched state.
  * lbm_step on a batched state takes force = host double[n_beds][3];
- *   lbm_reduce_flux writes mass_out[n_beds] and flux_out[n_beds].  The K
+ *   lbm_reduce_flux writes mass_out[n_beds] and flux_out[n_beds].  The
  *   launches of one lbm_step call are captured once into a CUDA graph and
- *   replayed while K, the relaxation rates and the launch shape stay the
- *   same (forces may change between calls).
+ *   replayed while K, the relaxation rates, the launch shape and the L2
+ *   groups (lbm_batch_groups) stay the same (forces may change between
+ *   calls).
  */
 int lbm_state_create_batched(const lbm_sparse* const* beds, int32_t n_beds, int32_t precision,
                              int32_t scale_exp, lbm_state** out);
@@ -289,6 +290,19 @@ int lbm_batch_layout(const lbm_state* st, int32_t* n_beds, int64_t* begin_out,
 /* Launch shape of the non-reducing steps: block in {128, 256, 512}, cells
  * per thread in {1, 2, 4}; use_graph 0/1.  Results do not depend on it. */
 int lbm_batch_config(lbm_state* st, int32_t block, int32_t cells_per_thread, int32_t use_graph);
+
+/* L2 groups.  The beds, in layout order, are split into groups whose working
+ * set (both PDF grids and the adjacency of their padded cells) fits `bytes`;
+ * a bed larger than that forms a group of its own.  An lbm_step call then
+ * runs all its steps on the first group, then on the next, so that each
+ * group streams from L2 instead of HBM.  With one group every launch steps
+ * all beds.  Either way a call of K steps is captured into a CUDA graph
+ * (use_graph) when groups x K <= 2^18 launches, and otherwise launched
+ * directly.  bytes = 0: one group; bytes < 0: the
+ * default, 0.6 of the device's L2 (set at creation).  *n_groups_out (may be
+ * NULL) receives the number of groups.  Results do not depend on it: beds
+ * are independent, and each bed takes the same steps in the same order. */
+int lbm_batch_groups(lbm_state* st, int64_t bytes, int32_t* n_groups_out);
 
 /* Autotuner: times steps_per_candidate steps under each of the nine launch
  * shapes (advancing the state by 9 * (steps_per_candidate + 1) steps, whose

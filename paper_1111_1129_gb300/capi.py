@@ -50,6 +50,7 @@ SIGNATURES = {
     "lbm_state_create_batched": (ctypes.c_int, [_vp, _i32, _i32, _i32, _vp]),
     "lbm_batch_layout": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "lbm_batch_config": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
+    "lbm_batch_groups": (ctypes.c_int, [_vp, _i64, _vp]),
     "lbm_batch_tune": (ctypes.c_int, [_vp, _i32, _d, _d, _vp, _vp, _vp, _vp]),
     "lbm_halo_gather": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i32, _vp]),
     "lbm_adjoint_create": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
@@ -209,6 +210,14 @@ def lbm_batch_layout(state: int):
 
 def lbm_batch_config(state: int, block: int, cells_per_thread: int, use_graph: bool) -> None:
     _check(load().lbm_batch_config(state, int(block), int(cells_per_thread), int(bool(use_graph))))
+
+
+def lbm_batch_groups(state: int, nbytes: int) -> int:
+    """Set the L2 group budget in bytes (0: one group; < 0: the default);
+    returns the number of groups."""
+    g = ctypes.c_int32(0)
+    _check(load().lbm_batch_groups(state, int(nbytes), ctypes.byref(g)))
+    return g.value
 
 
 def _forces(forces):

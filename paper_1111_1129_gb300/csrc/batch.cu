@@ -55,11 +55,18 @@ __global__ void __launch_bounds__(512)
                        int32_t n, Coef<typename Form<PREC>::C> k,
                        const BedForce<typename Form<PREC>::C>* __restrict__ forces,
                        const int32_t* __restrict__ chunk_bed, const int64_t* __restrict__ begin,
-                       const int32_t* __restrict__ count, double* __restrict__ partials) {
+                       const int32_t* __restrict__ count, int64_t cell0,
+                       double* __restrict__ partials) {
   using C = typename Form<PREC>::C;
-  const int64_t base = (int64_t)blockIdx.x * blockDim.x * CPT;
-  const int bed = chunk_bed[base / kBatchChunk];
-  const int64_t end = begin[bed] + count[bed];
+  // A chained launch waits here for the previous step.  The zero it returns
+  // offsets every index and the sums pointer, so no access is scheduled
+  // ahead of the wait.
+  const int32_t z = prior_step_done();
+  // src, dst and adj are the group's arrays, n its padded length; `base` is
+  // local to the group, cell0 + base the padded index in the whole list
+  const int64_t base = (int64_t)blockIdx.x * blockDim.x * CPT + z;
+  const int bed = chunk_bed[(cell0 + base) / kBatchChunk];
+  const int64_t end = begin[bed] + count[bed] - cell0;
   Coef<C> kb = k;
   const BedForce<C> bf = forces[bed];
 #pragma unroll
@@ -86,7 +93,7 @@ __global__ void __launch_bounds__(512)
   if constexpr (REDUCE) {   // runs with 256 threads and CPT = 1
     double w[4];
     warp_flux_sums<C, Form<PREC>::kShifted>(live, rho, u, w);
-    store_warp_sums(w, partials);
+    store_warp_sums(w, partials + z);
   }
 }
 
@@ -119,40 +126,169 @@ __global__ void __launch_bounds__(1024)
   if (threadIdx.x < 4) out[4 * bed + threadIdx.x] = sm[0][threadIdx.x];
 }
 
+// ---- group layout ------------------------------------------------------------
+// A layout on the device: the group of each 2048-cell chunk and each group's
+// first padded cell and length; chunk_group null: one group of all cells.
+struct GroupLayout {
+  const int32_t* chunk_group;
+  const int64_t* cell0;
+  const int64_t* span;
+};
+
+__device__ __forceinline__ void group_of(const GroupLayout& L, int64_t i, int64_t n, int64_t& c0,
+                                         int64_t& span) {
+  if (!L.chunk_group) {
+    c0 = 0;
+    span = n;
+    return;
+  }
+  const int g = L.chunk_group[i / kBatchChunk];
+  c0 = L.cell0[g];
+  span = L.span[g];
+}
+
+// dst in layout `to` = src in layout `from`, element (q, i) for q < 19.
+template <class T>
+__global__ void relayout_pdfs_kernel(const T* __restrict__ src, T* __restrict__ dst, int64_t n,
+                                     GroupLayout from, GroupLayout to) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 19 * n) return;
+  const int64_t q = e / n, i = e - q * n;
+  int64_t ca, sa, cb, sb;
+  group_of(from, i, n, ca, sa);
+  group_of(to, i, n, cb, sb);
+  dst[19 * cb + q * sb + (i - cb)] = src[19 * ca + q * sa + (i - ca)];
+}
+
+// The links in layout `to` from those in layout `from`: a link is a slot
+// q' * span + j local to the cell's group, and the pulled cell c0 + j lies in
+// the same bed, hence in the same group of either layout.
+__global__ void relayout_adj_kernel(const int32_t* __restrict__ src, int32_t* __restrict__ dst,
+                                    int64_t n, GroupLayout from, GroupLayout to) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 18 * n) return;
+  const int64_t r = e / n, i = e - r * n;
+  int64_t ca, sa, cb, sb;
+  group_of(from, i, n, ca, sa);
+  group_of(to, i, n, cb, sb);
+  const int64_t v = src[18 * ca + r * sa + (i - ca)];
+  const int64_t q = v / sa, j = v - q * sa;
+  dst[18 * cb + r * sb + (i - cb)] = (int32_t)(q * sb + (ca + j - cb));
+}
+
+GroupLayout layout_of(const Batch* b) {
+  if (b->group_cell0.size() <= 1) return GroupLayout{nullptr, nullptr, nullptr};
+  return GroupLayout{b->d_chunk_group, b->d_group_cell0, b->d_group_span};
+}
+
+int relayout_pdfs(const lbm_state* st, int from_buf, int to_buf, GroupLayout from,
+                  GroupLayout to) {
+  const int64_t n = st->sp->n;
+  if (n == 0) return LBM_OK;
+  const unsigned grid = (unsigned)((19 * n + 255) / 256);
+  const cudaStream_t stream = st->sp->stream;
+  switch (storage_bytes(st->precision)) {
+    case 2:
+      relayout_pdfs_kernel<uint16_t><<<grid, 256, 0, stream>>>(
+          (const uint16_t*)st->buf[from_buf], (uint16_t*)st->buf[to_buf], n, from, to);
+      break;
+    case 4:
+      relayout_pdfs_kernel<uint32_t><<<grid, 256, 0, stream>>>(
+          (const uint32_t*)st->buf[from_buf], (uint32_t*)st->buf[to_buf], n, from, to);
+      break;
+    default:
+      relayout_pdfs_kernel<uint64_t><<<grid, 256, 0, stream>>>(
+          (const uint64_t*)st->buf[from_buf], (uint64_t*)st->buf[to_buf], n, from, to);
+  }
+  LBM_CUDA_TRY(cudaGetLastError());
+  return LBM_OK;
+}
+
+// One step of the padded cells [cell0, cell0 + span) (whole beds, span a
+// multiple of kBatchChunk).  `chained`: the previous launch on the stream is
+// a step of the same call (not in FP64 arithmetic, which chaining slows
+// down; see lbm_step).
 template <int PREC, bool REDUCE>
-void launch_one(lbm_state* st, int block, int cpt, cudaStream_t stream,
-                const Coef<typename Form<PREC>::C>& k) {
+cudaError_t launch_one(lbm_state* st, int block, int cpt, cudaStream_t stream,
+                       const Coef<typename Form<PREC>::C>& k, bool chained, int64_t cell0,
+                       int64_t span) {
   using S = typename Form<PREC>::S;
   using C = typename Form<PREC>::C;
   Batch* b = st->batch;
-  const int32_t n = (int32_t)st->sp->n;
-  const S* src = (const S*)st->buf[st->cur];
-  S* dst = (S*)st->buf[st->cur ^ 1];
-  const unsigned grid = (unsigned)(n / (block * cpt));
+  const int32_t n = (int32_t)span;
+  const S* src = (const S*)st->buf[st->cur] + 19 * cell0;
+  S* dst = (S*)st->buf[st->cur ^ 1] + 19 * cell0;
+  const int32_t* adj = st->sp->adj + 18 * cell0;
+  const unsigned grid = (unsigned)(span / (block * cpt));
   const BedForce<C>* forces = (const BedForce<C>*)b->d_force;
+  const bool pdl = chained && PREC != LBM_F64 && PREC != LBM_F64X;
+  // the reducing step's warp slots are indexed by global 256-cell block
+  double* partials = st->partials + 4 * kWarpsPerBlock * (cell0 / kSweepThreads);
 #define LBM_BATCH_LAUNCH(CPT)                                                          \
-  batch_sweep_kernel<PREC, REDUCE, CPT><<<grid, block, 0, stream>>>(                   \
-      src, dst, st->sp->adj, n, k, forces, b->d_chunk_bed, b->d_begin, b->d_count,     \
-      st->partials)
-  if (cpt == 1) LBM_BATCH_LAUNCH(1);
-  else if (cpt == 2) LBM_BATCH_LAUNCH(2);
-  else LBM_BATCH_LAUNCH(4);
+  launch_chained(batch_sweep_kernel<PREC, REDUCE, CPT>, grid, (unsigned)block, stream, pdl, \
+                 src, dst, adj, n, k, forces,                                          \
+                 (const int32_t*)b->d_chunk_bed, (const int64_t*)b->d_begin,           \
+                 (const int32_t*)b->d_count, cell0, partials)
+  cudaError_t e;
+  if (cpt == 1) e = LBM_BATCH_LAUNCH(1);
+  else if (cpt == 2) e = LBM_BATCH_LAUNCH(2);
+  else e = LBM_BATCH_LAUNCH(4);
 #undef LBM_BATCH_LAUNCH
   st->cur ^= 1;
+  return e;
 }
 
-// Enqueues n_steps steps on `stream` (the last one reduces).
+// Enqueues n_steps steps of the cells [cell0, cell0 + span) on `stream`
+// (the last one reduces); the first launch is chained when `chain_first`.
 template <int PREC>
-void enqueue_steps(lbm_state* st, int32_t n_steps, double wp, double wm, int block, int cpt,
-                   cudaStream_t stream) {
+cudaError_t enqueue_steps(lbm_state* st, int32_t n_steps, double wp, double wm, int block,
+                          int cpt, cudaStream_t stream, int64_t cell0, int64_t span,
+                          bool chain_first) {
   using C = typename Form<PREC>::C;
   const double zero[3] = {0.0, 0.0, 0.0};
   const Coef<C> k = make_coef<C>(wp, wm, zero, st->scale_exp);
+  cudaError_t err = cudaSuccess;
   for (int32_t t = 0; t < n_steps; ++t) {
-    if (t == n_steps - 1) launch_one<PREC, true>(st, kSweepThreads, 1, stream, k);
-    else launch_one<PREC, false>(st, block, cpt, stream, k);
+    const bool chained = t > 0 || chain_first;
+    const cudaError_t e =
+        t == n_steps - 1
+            ? launch_one<PREC, true>(st, kSweepThreads, 1, stream, k, chained, cell0, span)
+            : launch_one<PREC, false>(st, block, cpt, stream, k, chained, cell0, span);
+    if (err == cudaSuccess) err = e;
   }
+  return err;
 }
+
+// All steps of one group, then of the next: every group starts from the
+// call's parity and ends at parity ^ (n_steps & 1).
+template <int PREC>
+cudaError_t enqueue_grouped(lbm_state* st, int32_t n_steps, double wp, double wm,
+                            cudaStream_t stream) {
+  Batch* b = st->batch;
+  const int parity = st->cur;
+  cudaError_t err = cudaSuccess;
+  for (size_t g = 0; g < b->group_cell0.size(); ++g) {
+    st->cur = parity;
+    const cudaError_t e = enqueue_steps<PREC>(st, n_steps, wp, wm, b->block, b->cpt, stream,
+                                              b->group_cell0[g], b->group_span[g], g > 0);
+    if (err == cudaSuccess) err = e;
+  }
+  st->cur = parity ^ (n_steps & 1);
+  return err;
+}
+
+// The launches of one call: grouped, or every step over all beds.
+template <int PREC>
+cudaError_t enqueue_call(lbm_state* st, int32_t n_steps, double wp, double wm,
+                         cudaStream_t stream) {
+  Batch* b = st->batch;
+  if (b->group_cell0.size() > 1) return enqueue_grouped<PREC>(st, n_steps, wp, wm, stream);
+  return enqueue_steps<PREC>(st, n_steps, wp, wm, b->block, b->cpt, stream, 0, st->sp->n, false);
+}
+
+// Largest graph (kernel nodes) a call is captured into; longer calls launch
+// their kernels one by one.
+constexpr int64_t kMaxBatchGraphNodes = 1 << 18;
 
 template <int PREC>
 int fill_forces(lbm_state* st, double wm, const double* forces, cudaStream_t stream) {
@@ -184,14 +320,14 @@ int run_batch(lbm_state* st, int32_t n_steps, double wp, double wm, const double
     st->cur ^= (n_steps & 1);
     return LBM_OK;
   }
-  if (!b->use_graph) {
-    enqueue_steps<PREC>(st, n_steps, wp, wm, b->block, b->cpt, stream);
-    LBM_CUDA_TRY(cudaGetLastError());
+  const int64_t nodes = (int64_t)b->group_cell0.size() * n_steps;
+  if (!b->use_graph || nodes > kMaxBatchGraphNodes) {
+    LBM_CUDA_TRY(enqueue_call<PREC>(st, n_steps, wp, wm, stream));
     return LBM_OK;
   }
   const bool hit = b->graph && b->g_steps == n_steps && b->g_parity == st->cur &&
                    b->g_block == b->block && b->g_cpt == b->cpt && b->g_wp == wp &&
-                   b->g_wm == wm;
+                   b->g_wm == wm && b->g_group_bytes == b->group_bytes;
   if (!hit) {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
@@ -199,10 +335,14 @@ int run_batch(lbm_state* st, int32_t n_steps, double wp, double wm, const double
     }
     const int parity = st->cur;
     LBM_CUDA_TRY(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
-    enqueue_steps<PREC>(st, n_steps, wp, wm, b->block, b->cpt, b->capture);
+    const cudaError_t el = enqueue_call<PREC>(st, n_steps, wp, wm, b->capture);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->capture, &g);
     st->cur = parity;  // capture only recorded the launches
+    if (el != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(el, "batch step launch under capture");
+    }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     const cudaError_t e2 = cudaGraphInstantiate(&b->graph, g, 0);
     cudaGraphDestroy(g);
@@ -216,6 +356,7 @@ int run_batch(lbm_state* st, int32_t n_steps, double wp, double wm, const double
     b->g_cpt = b->cpt;
     b->g_wp = wp;
     b->g_wm = wm;
+    b->g_group_bytes = b->group_bytes;
   }
   LBM_CUDA_TRY(cudaGraphLaunch(b->graph, stream));
   st->cur ^= (n_steps & 1);
@@ -241,7 +382,144 @@ size_t dispatch_force_bytes(int prec) { LBM_BATCH_DISPATCH(prec, force_bytes) }
 
 bool valid_batch(const lbm_state* st) { return valid_state(st) && st->batch; }
 
+// Splits the beds, in layout order, into groups whose working set (two PDF
+// grids and the adjacency, per padded cell) fits `bytes`; a bed larger than
+// that is a group of its own.  bytes <= 0: one group of all beds.
+void split_groups(const lbm_state* st, int64_t bytes, std::vector<int64_t>& cell0_out,
+                  std::vector<int64_t>& span_out) {
+  const Batch* b = st->batch;
+  cell0_out.clear();
+  span_out.clear();
+  const int64_t n_pad = st->sp->n;
+  if (bytes <= 0 || n_pad == 0) {
+    cell0_out.push_back(0);
+    span_out.push_back(n_pad);
+    return;
+  }
+  const int64_t per_cell = 2 * 19 * (int64_t)storage_bytes(st->precision) + 18 * 4;
+  int64_t cell0 = 0, span = 0;
+  for (int i = 0; i < b->n_beds; ++i) {
+    const int64_t s = (b->h_count[i] + kBatchChunk - 1) / kBatchChunk * kBatchChunk;
+    if (s == 0) continue;
+    if (span > 0 && (span + s) * per_cell > bytes) {
+      cell0_out.push_back(cell0);
+      span_out.push_back(span);
+      cell0 = b->h_begin[i];
+      span = 0;
+    }
+    span += s;
+  }
+  cell0_out.push_back(cell0);
+  span_out.push_back(span);
+}
+
+void free_group_tables(Batch* b) {
+  for (void* p : {(void*)b->d_chunk_group, (void*)b->d_group_cell0, (void*)b->d_group_span})
+    if (p) cudaFree(p);
+  b->d_chunk_group = nullptr;
+  b->d_group_cell0 = nullptr;
+  b->d_group_span = nullptr;
+}
+
+// Sets the L2 groups for a budget of `bytes` and moves the current PDFs and
+// the links into their layout (the other PDF grid is scratch).  Allocates
+// the new group tables and a second link array while it runs.
+int regroup(lbm_state* st, int64_t bytes) {
+  Batch* b = st->batch;
+  std::vector<int64_t> c0, span;
+  split_groups(st, bytes, c0, span);
+  b->group_bytes = bytes > 0 ? bytes : 0;
+  if (c0 == b->group_cell0 && span == b->group_span) return LBM_OK;
+  const cudaStream_t stream = st->sp->stream;
+  const int64_t n = st->sp->n;
+  const GroupLayout from = layout_of(b);
+  // new tables
+  int32_t* d_chunk_group = nullptr;
+  int64_t *d_c0 = nullptr, *d_span = nullptr;
+  int32_t* adj_new = nullptr;
+  const size_t G = c0.size();
+  std::vector<int32_t> chunk_group((size_t)(n / kBatchChunk > 0 ? n / kBatchChunk : 1), 0);
+  for (size_t g = 0; g < G; ++g)
+    for (int64_t c = c0[g] / kBatchChunk; c < (c0[g] + span[g]) / kBatchChunk; ++c)
+      chunk_group[(size_t)c] = (int32_t)g;
+  bool ok = cudaMalloc(&adj_new, sizeof(int32_t) * 18 * (size_t)(n > 0 ? n : 1)) == cudaSuccess;
+  if (ok && G > 1)
+    ok = cudaMalloc(&d_chunk_group, sizeof(int32_t) * chunk_group.size()) == cudaSuccess &&
+         cudaMalloc(&d_c0, sizeof(int64_t) * G) == cudaSuccess &&
+         cudaMalloc(&d_span, sizeof(int64_t) * G) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    for (void* p : {(void*)d_chunk_group, (void*)d_c0, (void*)d_span, (void*)adj_new})
+      if (p) cudaFree(p);
+    return fail(LBM_ENOMEM, "allocation for the L2 group layout failed");
+  }
+  cudaError_t e = cudaSuccess;
+  if (G > 1) {
+    e = cudaMemcpyAsync(d_chunk_group, chunk_group.data(), sizeof(int32_t) * chunk_group.size(),
+                        cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_c0, c0.data(), sizeof(int64_t) * G, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_span, span.data(), sizeof(int64_t) * G, cudaMemcpyHostToDevice,
+                          stream);
+  }
+  const GroupLayout to = G > 1 ? GroupLayout{d_chunk_group, d_c0, d_span}
+                               : GroupLayout{nullptr, nullptr, nullptr};
+  int rc = LBM_OK;
+  if (e == cudaSuccess && n > 0) {
+    rc = relayout_pdfs(st, st->cur, st->cur ^ 1, from, to);
+    relayout_adj_kernel<<<(unsigned)((18 * n + 255) / 256), 256, 0, stream>>>(
+        st->sp->adj, adj_new, n, from, to);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess || rc != LBM_OK) {
+    for (void* p : {(void*)d_chunk_group, (void*)d_c0, (void*)d_span, (void*)adj_new})
+      if (p) cudaFree(p);
+    return rc != LBM_OK ? rc : cuda_fail(e, "L2 group relayout");
+  }
+  // the cached graph holds the old link array
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  lbm_sparse* sp = const_cast<lbm_sparse*>(st->sp);
+  cudaFree(sp->adj);
+  sp->adj = adj_new;
+  st->cur ^= 1;
+  free_group_tables(b);
+  b->d_chunk_group = d_chunk_group;
+  b->d_group_cell0 = d_c0;
+  b->d_group_span = d_span;
+  b->group_cell0 = c0;
+  b->group_span = span;
+  return LBM_OK;
+}
+
+// Default group budget: 0.6 of the L2 (77 MB of GB300's 129 MB).  On 256
+// beds of 34.6 M cells in all (FP32 shifted), budgets of 64 and 96 MiB ran
+// at 39,500 and 40,000 MFLUP/s, 128 MiB at 32,500, and one group at 31,400.
+int64_t default_group_bytes() {
+  int dev = 0, l2 = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (int64_t)(0.6 * (double)l2);
+}
+
 }  // namespace
+
+bool batch_grouped(const lbm_state* st) {
+  return st->batch && st->batch->group_cell0.size() > 1;
+}
+
+int batch_relayout_pdfs(const lbm_state* st, int from, int to, bool to_plain) {
+  const GroupLayout plain{nullptr, nullptr, nullptr}, grouped = layout_of(st->batch);
+  return to_plain ? relayout_pdfs(st, from, to, grouped, plain)
+                  : relayout_pdfs(st, from, to, plain, grouped);
+}
 
 int batch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const double* forces) {
   LBM_BATCH_DISPATCH(st->precision, run_batch, st, n_steps, wp, wm, forces)
@@ -282,6 +560,7 @@ void free_batch(lbm_state* st) {
   for (void* p : {(void*)b->d_begin, (void*)b->d_count, (void*)b->d_chunk_bed, b->d_force,
                   (void*)b->d_red})
     if (p) cudaFree(p);
+  free_group_tables(b);
   for (void* p : {b->h_force, (void*)b->h_red})
     if (p) cudaFreeHost(p);
   delete[] b->h_begin;
@@ -367,6 +646,8 @@ extern "C" int lbm_state_create_batched(const lbm_sparse* const* beds, int32_t n
   b->block = kSweepThreads;
   b->cpt = 1;
   b->use_graph = 1;
+  b->group_cell0.assign(1, 0);
+  b->group_span.assign(1, total);
   const size_t fbytes = dispatch_force_bytes(precision);
   bool ok = cudaMalloc(&b->d_begin, sizeof(int64_t) * n_beds) == cudaSuccess &&
             cudaMalloc(&b->d_count, sizeof(int32_t) * n_beds) == cudaSuccess &&
@@ -391,6 +672,11 @@ extern "C" int lbm_state_create_batched(const lbm_sparse* const* beds, int32_t n
   if (e != cudaSuccess) {
     free_state(st);
     return cuda_fail(e, "batch tables upload");
+  }
+  rc = regroup(st, default_group_bytes());
+  if (rc != LBM_OK) {
+    free_state(st);
+    return rc;
   }
   *out = st;
   return LBM_OK;
@@ -421,6 +707,15 @@ extern "C" int lbm_batch_config(lbm_state* st, int32_t block, int32_t cells_per_
   st->batch->block = block;
   st->batch->cpt = cells_per_thread;
   st->batch->use_graph = use_graph != 0;
+  return LBM_OK;
+}
+
+extern "C" int lbm_batch_groups(lbm_state* st, int64_t bytes, int32_t* n_groups_out) {
+  clear_error();
+  if (!valid_batch(st)) return fail(LBM_EINVAL, "not a batched state");
+  const int rc = regroup(st, bytes < 0 ? default_group_bytes() : bytes);
+  if (rc != LBM_OK) return rc;
+  if (n_groups_out) *n_groups_out = (int32_t)st->batch->group_cell0.size();
   return LBM_OK;
 }
 

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 #include "lbm.h"
 
@@ -256,6 +257,19 @@ struct Batch {
   int32_t g_steps, g_parity, g_block, g_cpt;
   double g_wp, g_wm;
   int use_graph;
+  // L2 groups: consecutive beds whose working set (both PDF grids and the
+  // adjacency) fits group_bytes.  With more than one group, a call runs all
+  // its steps on one group, then on the next, so each group's steps stream
+  // from L2 rather than HBM.  group_bytes 0: one group of all beds.
+  // Each group's arrays are contiguous: the PDFs of its padded cells
+  // [c0, c0 + span) are 19 rows of span at offset 19 c0, its links 18 rows
+  // at 18 c0, holding slots local to the group.  One group is the plain
+  // [19][N_pad] layout that lbm_state_get/set_pdfs present.
+  int64_t group_bytes, g_group_bytes;  // current; the cached graph's
+  std::vector<int64_t> group_cell0, group_span;  // padded first cell and length
+  int32_t* d_chunk_group;  // [N_pad / kBatchChunk] group of each chunk (null: one group)
+  int64_t* d_group_cell0;  // [groups]
+  int64_t* d_group_span;   // [groups]
 };
 
 // Single-state step graphs: kGraphSteps non-reducing steps captured once per
@@ -280,20 +294,25 @@ struct StepGraph {
 #define LBM_CHAIN_STEPS 1
 #endif
 template <class... P, class... A>
-cudaError_t launch_sweep(void (*kernel)(P...), unsigned grid, cudaStream_t stream, bool chained,
-                         A... args) {
+cudaError_t launch_chained(void (*kernel)(P...), unsigned grid, unsigned block,
+                           cudaStream_t stream, bool chained, A... args) {
   cudaLaunchAttribute attr;
   attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr.val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kSweepThreads);
+  cfg.blockDim = dim3(block);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = stream;
   const bool pdl = LBM_CHAIN_STEPS && chained;
   cfg.attrs = pdl ? &attr : nullptr;
   cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+template <class... P, class... A>
+cudaError_t launch_sweep(void (*kernel)(P...), unsigned grid, cudaStream_t stream, bool chained,
+                         A... args) {
+  return launch_chained(kernel, grid, (unsigned)kSweepThreads, stream, chained, args...);
 }
 }  // namespace lbm
 
@@ -339,4 +358,9 @@ int wait_event(cudaEvent_t ev, cudaStream_t stream, double timeout_s);
 int batch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const double* forces);
 int batch_reduce(lbm_state* st, int32_t axis, double* mass_out, double* flux_out);
 void free_batch(lbm_state* st);
+// True if a batched state's arrays are in a layout of several L2 groups.
+bool batch_grouped(const lbm_state* st);
+// Copies the PDFs of buf[from] into buf[to], from the group layout into the
+// plain [19][N_pad] one (to_plain) or back.
+int batch_relayout_pdfs(const lbm_state* st, int from, int to, bool to_plain);
 }  // namespace lbm

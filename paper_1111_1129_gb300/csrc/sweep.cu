@@ -159,14 +159,19 @@ int launch_moments(const lbm_state* st, double* rho, double* u) {
   return LBM_OK;
 }
 
+// A batched state in several L2 groups keeps its arrays in the group layout:
+// set and get go through the plain layout in the other PDF grid, which
+// holds nothing between the steps of a batched state.
 template <int PREC>
 int launch_set(lbm_state* st, const double* f, int from_rest) {
   const int64_t total = 19 * st->sp->n;
   if (total == 0) return LBM_OK;
+  const bool grouped = batch_grouped(st);
   set_pdfs_kernel<PREC><<<(unsigned)((total + 255) / 256), 256, 0, st->sp->stream>>>(
-      (typename Form<PREC>::S*)st->buf[st->cur], f, (int32_t)st->sp->n,
+      (typename Form<PREC>::S*)st->buf[grouped ? st->cur ^ 1 : st->cur], f, (int32_t)st->sp->n,
       std::ldexp(1.0, st->scale_exp), from_rest);
   LBM_CUDA_TRY(cudaGetLastError());
+  if (grouped) return batch_relayout_pdfs(st, st->cur ^ 1, st->cur, false);
   return LBM_OK;
 }
 
@@ -174,9 +179,14 @@ template <int PREC>
 int launch_get(const lbm_state* st, double* f) {
   const int64_t total = 19 * st->sp->n;
   if (total == 0) return LBM_OK;
+  const bool grouped = batch_grouped(st);
+  if (grouped) {
+    const int rc = batch_relayout_pdfs(st, st->cur, st->cur ^ 1, true);
+    if (rc != LBM_OK) return rc;
+  }
   get_pdfs_kernel<PREC><<<(unsigned)((total + 255) / 256), 256, 0, st->sp->stream>>>(
-      (const typename Form<PREC>::S*)st->buf[st->cur], f, (int32_t)st->sp->n,
-      std::ldexp(1.0, -st->scale_exp));
+      (const typename Form<PREC>::S*)st->buf[grouped ? st->cur ^ 1 : st->cur], f,
+      (int32_t)st->sp->n, std::ldexp(1.0, -st->scale_exp));
   LBM_CUDA_TRY(cudaGetLastError());
   return LBM_OK;
 }

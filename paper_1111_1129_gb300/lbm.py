@@ -344,6 +344,12 @@ class BatchedState:
     def configure(self, block: int = 256, cells_per_thread: int = 1, use_graph: bool = True):
         capi.lbm_batch_config(self._handle, block, cells_per_thread, use_graph)
 
+    def groups(self, nbytes: int = -1) -> int:
+        """Step the beds in L2-sized groups of at most `nbytes` working set
+        (0: all beds in every launch; < 0: the default, 0.6 of the L2);
+        returns the number of groups.  Results do not depend on it."""
+        return capi.lbm_batch_groups(self._handle, nbytes)
+
     def tune(self, steps_per_candidate: int, omega_plus: float, omega_minus: float, forces):
         """Pick the fastest launch shape (advances the state)."""
         return capi.lbm_batch_tune(self._handle, steps_per_candidate, omega_plus, omega_minus,

@@ -1,6 +1,7 @@
 """Batched beds (one launch per step over concatenated cell lists, per-bed
-forces, CUDA graph, tuned launch shape): every bed's PDFs and flux must be
-bit-identical to stepping that bed alone, whatever the launch shape."""
+forces, CUDA graph, tuned launch shape, L2 groups of beds stepped one group
+at a time): every bed's PDFs and flux must be bit-identical to stepping that
+bed alone, whatever the launch shape and the grouping."""
 import numpy as np
 import pytest
 import torch
@@ -51,9 +52,17 @@ def test_batched_beds_bit_identical_to_separate_runs(precision):
         ref_f.append(st.get_pdfs().cpu().numpy())
         ref_flux.append(st.reduce_flux(2) if lat.n > 0 else None)
         st.close()
-    for block, cpt, graph in [(256, 1, True), (128, 4, True), (512, 2, False), (512, 4, True)]:
+    for block, cpt, graph, group_bytes in [(256, 1, True, 0), (128, 4, True, 0),
+                                           (512, 2, False, 0), (512, 4, True, 0),
+                                           (256, 1, True, 1), (256, 2, True, 3 << 20),
+                                           (512, 4, False, 1 << 20)]:
         bs = BatchedState(lats, precision, 20)
         bs.configure(block, cpt, graph)
+        n_groups = bs.groups(group_bytes)
+        if group_bytes == 0:
+            assert n_groups == 1
+        if group_bytes == 1:
+            assert n_groups == sum(1 for lat in lats if lat.n > 0)
         bs.step(steps, WP, WM, forces)
         mass, flux = bs.reduce_flux(2)
         f_all = bs.get_pdfs().cpu().numpy()
@@ -65,6 +74,35 @@ def test_batched_beds_bit_identical_to_separate_runs(precision):
                 assert (mass[i], flux[i]) == ref_flux[i]
             else:
                 assert (mass[i], flux[i]) == (0.0, 0.0)
+        bs.close()
+    for lat in lats:
+        lat.close()
+
+
+def test_group_split_follows_the_budget():
+    """Groups are runs of consecutive beds whose padded cells times the bytes
+    per cell (two PDF grids and 18 int32 links) fit the budget; a bed above
+    it is alone; an empty bed joins no group."""
+    beds, _ = _beds(7, seed=5)
+    lats = _lattices(beds)
+    for precision, per_cell in (("f32s", 2 * 19 * 4 + 72), ("f16s", 2 * 19 * 2 + 72),
+                                ("f64", 2 * 19 * 8 + 72)):
+        bs = BatchedState(lats, precision, 20)
+        spans = [(c + 2047) // 2048 * 2048 for c in bs.count]
+        for budget in (1, 2048 * per_cell, 3 * 2048 * per_cell, 10 * 2048 * per_cell, 0):
+            expect, cur = 0, 0
+            for s_ in spans:
+                if s_ == 0:
+                    continue
+                if cur > 0 and (cur + s_) * per_cell > budget:
+                    expect += 1
+                    cur = 0
+                cur += s_
+            expect += 1
+            if budget == 0:
+                expect = 1
+            assert bs.groups(budget) == expect, (precision, budget)
+        assert bs.groups(-1) >= 1
         bs.close()
     for lat in lats:
         lat.close()
@@ -107,19 +145,23 @@ def test_tuner_picks_a_candidate_and_keeps_results():
         lat.close()
 
 
-def test_full_batch_of_256_beds_sampled():
+@pytest.mark.parametrize("group_bytes", [0, -1])
+def test_full_batch_of_256_beds_sampled(group_bytes):
     """The 256-bed workload (cube sides uniform in {24..96}, radii in [3, 8],
-    forces in [1e-7, 1e-5] along z), FP32 shifted storage, 1000 steps as one
-    graph: per-bed flux of 8 sampled beds equals their separate runs."""
+    forces in [1e-7, 1e-5] along z), FP32 shifted storage, 1000 steps, as one
+    graph (one group) and in the default L2 groups: per-bed flux of 8
+    sampled beds equals their separate runs."""
     beds, fz = inputs.batch_beds(256, 0)
     forces = [(0.0, 0.0, float(f)) for f in fz]
     lats = _lattices(beds)
     bs = BatchedState(lats, "f32s")
     bs.configure(256, 2, True)
+    n_groups = bs.groups(group_bytes)
+    assert (n_groups == 1) == (group_bytes == 0)
     bs.step(1000, WP, WM, forces)
     mass, flux = bs.reduce_flux(2)
     assert bs.n_fluid == sum(b.n_fluid for b in beds)
-    rng = np.random.default_rng(0)
+    rng = np.random.default_rng(group_bytes + 1)
     for i in rng.choice(256, 8, replace=False):
         st = LBMState(lats[i], "f32s")
         st.step(1000, WP, WM, forces[i])
