@@ -179,7 +179,12 @@ int lbm_set_damping(lbm_state* st, const double* alpha_dev);
  * (per grid parity and per set of rates, force and damping pointer) and
  * keeps until lbm_free; the kernels and results are those of launching
  * every step, and a stream that is itself being captured gets plain
- * launches.  Errors: LBM_EINVAL, LBM_ECUDA.
+ * launches.  The second and later steps of a call (in FP32, 16-bit and
+ * fixed-point FP64-storage arithmetic) are launched with programmatic
+ * dependent launch: their blocks start while the previous step ends and
+ * wait in the kernel for it, which changes no result.  The first step of a
+ * call waits for all earlier work on the stream as usual.  Errors:
+ * LBM_EINVAL, LBM_ECUDA.
  */
 int lbm_step(lbm_state* st, int32_t n_steps, double omega_plus, double omega_minus,
              const double force[3]);
