@@ -468,11 +468,15 @@ int regroup(lbm_state* st, int64_t bytes) {
   int rc = LBM_OK;
   if (e == cudaSuccess && n > 0) {
     rc = relayout_pdfs(st, st->cur, st->cur ^ 1, from, to);
-    relayout_adj_kernel<<<(unsigned)((18 * n + 255) / 256), 256, 0, stream>>>(
-        st->sp->adj, adj_new, n, from, to);
-    e = cudaGetLastError();
+    if (rc == LBM_OK) {
+      relayout_adj_kernel<<<(unsigned)((18 * n + 255) / 256), 256, 0, stream>>>(
+          st->sp->adj, adj_new, n, from, to);
+      e = cudaGetLastError();
+    }
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  // whatever was queued finishes before anything is freed
+  const cudaError_t es = cudaStreamSynchronize(stream);
+  if (e == cudaSuccess) e = es;
   if (e != cudaSuccess || rc != LBM_OK) {
     for (void* p : {(void*)d_chunk_group, (void*)d_c0, (void*)d_span, (void*)adj_new})
       if (p) cudaFree(p);
