@@ -6,7 +6,8 @@
 // block x cells-per-thread <= 2048 cells lies inside one bed and finds its
 // bed from a per-chunk table -- no per-cell bed id is stored or read.  The
 // adjacency is remapped to the concatenated slots (q*N + m of a bed becomes
-// q*N_pad + begin + m); padding cells bounce every link onto themselves and
+// q*N_pad + begin + m, before the L2 groups below relayout it); padding
+// cells bounce every link onto themselves and
 // are never read or written by the sweep.  Each bed has its own body force,
 // taken from a small table.  The step that reduces runs with the 256-thread,
 // one-cell-per-thread layout of the single-bed sweep and reduces each bed
@@ -15,8 +16,17 @@
 //
 // Launch shape: the non-reducing steps use (block, cells per thread) from
 // {128, 256, 512} x {1, 2, 4}, picked by lbm_batch_tune; all shapes give the
-// same per-cell arithmetic.  A sequence of K steps is captured once into a
+// same per-cell arithmetic.  The launches of a call are captured once into a
 // CUDA graph (on a private stream) and replayed on the caller's stream.
+//
+// L2 groups: the beds, in list order, form groups whose working set fits a
+// budget (by default 0.6 of the L2), and a call takes all its steps on one
+// group before the next, so that a group's steps stream from L2.  Each
+// group keeps its arrays contiguous -- 19 PDF rows and 18 link rows of its
+// own padded length, links holding group-local slots -- and lbm_state_get/
+// set_pdfs convert to and from the plain [19][N_pad] layout.  Beds are
+// independent and every bed takes the same steps in the same order, so the
+// grouping changes no result.
 #include <cmath>
 #include <vector>
 
