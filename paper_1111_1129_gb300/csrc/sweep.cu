@@ -15,6 +15,8 @@
 //   store    f'[q][n] with streaming (evict-first) stores, the GPU analogue
 //            of the paper's nontemporal stores.
 // The last step of a call also reduces rho and u to per-warp FP64 sums.
+// The steps of a call after its first are chained (programmatic dependent
+// launch, except in FP64 arithmetic), and long calls replay CUDA graphs.
 //
 // Storage forms: FP64 / FP32 PDFs, or the deviation d_q = f_q - w_q from
 // the rest state in FP32, FP16 or BF16 (16-bit forms scaled by 2^k).  The
