@@ -38,7 +38,8 @@
  * the same thread).  No C++ exception crosses this interface.
  *
  * Device pointers are plain CUDA device addresses on the current device.
- * Handles (lbm_sparse, lbm_state) own device memory; they are released by
+ * Handles (lbm_sparse, lbm_state) own device memory, taken from the
+ * caller's allocator if one is set (lbm_set_allocator); they are released by
  * lbm_free.  A state refers to the sparse representation it was created
  * from, which must outlive it.  All work is queued on the stream given to
  * lbm_build_sparse (a cudaStream_t passed as void*, NULL = legacy default
@@ -47,6 +48,7 @@
 #ifndef LBM_GB300_H
 #define LBM_GB300_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -368,6 +370,25 @@ int lbm_adjoint_step(lbm_state* st, lbm_adjoint* adj, int32_t n_steps, double om
 /* Release a handle returned by this library (sparse, state or adjoint);
  * NULL is a no-op.  Waits for the handle's stream before freeing. */
 void lbm_free(void* handle);
+
+/* ---- device memory --------------------------------------------------------
+ * Handles take their device memory from a caller-supplied allocator when
+ * one is set, else from cudaMalloc (cudaMallocAsync on the handle's stream
+ * for the sparse representation and its scratch).
+ *   alloc(bytes, stream, ctx) returns a device pointer, or NULL: the calling
+ *     function then fails with LBM_ENOMEM.
+ *   release(ptr, stream, ctx) gives a block back.  It may be called while
+ *     work queued on `stream` still uses the block, so the allocator must not
+ *     hand the block to work on another stream before that work completes
+ *     (stream-ordered reuse, as in PyTorch's caching allocator).
+ * `stream` is the handle's stream (a cudaStream_t).  Set both functions, or
+ * neither for the library's own.  LBM_EINVAL if only one is given, or if
+ * blocks of existing handles are still live: a block goes back through the
+ * allocator that gave it, so free those handles first.  The setting is
+ * process-wide; do not change it while another thread uses the library. */
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*lbm_free_fn)(void* ptr, void* stream, void* ctx);
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void* ctx);
 
 /* Description of the last failure on this thread ("" if none). */
 const char* lbm_last_error(void);

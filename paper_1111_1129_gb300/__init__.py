@@ -10,7 +10,7 @@ error, never a fallback.
 """
 
 __all__ = ["SparseLattice", "LBMState", "Adjoint", "LBMFlux", "BatchedState", "omega_minus", "ordering_keys",
-           "deviation_bound", "shifted_scale_exp"]
+           "deviation_bound", "shifted_scale_exp", "use_torch_allocator"]
 
 
 def __getattr__(name):

@@ -25,6 +25,12 @@ _vp, _i32, _i64, _u32, _d = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ct
                              ctypes.c_double)
 
 
+# Allocator callbacks of lbm_set_allocator: alloc(bytes, stream, ctx) -> ptr,
+# release(ptr, stream, ctx).
+LBM_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+LBM_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class lbm_ordering(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("block", ctypes.c_int32 * 3),
                 ("periodic", ctypes.c_uint32)]
@@ -51,6 +57,7 @@ SIGNATURES = {
     "lbm_batch_layout": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "lbm_batch_config": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
     "lbm_batch_groups": (ctypes.c_int, [_vp, _i64, _vp]),
+    "lbm_set_allocator": (ctypes.c_int, [LBM_ALLOC_FN, LBM_FREE_FN, _vp]),
     "lbm_batch_tune": (ctypes.c_int, [_vp, _i32, _d, _d, _vp, _vp, _vp, _vp]),
     "lbm_halo_gather": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i32, _vp]),
     "lbm_adjoint_create": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
@@ -210,6 +217,33 @@ def lbm_batch_layout(state: int):
 
 def lbm_batch_config(state: int, block: int, cells_per_thread: int, use_graph: bool) -> None:
     _check(load().lbm_batch_config(state, int(block), int(cells_per_thread), int(bool(use_graph))))
+
+
+_allocator = None   # the callbacks in use, kept alive while the library holds them
+
+
+def lbm_set_allocator(alloc, release) -> None:
+    """Route the library's device memory through alloc(nbytes, stream) -> ptr
+    and release(ptr, stream) (Python callables; stream is a cudaStream_t as
+    int or None), or back to cudaMalloc with (None, None)."""
+    global _allocator
+    if alloc is None and release is None:
+        _check(load().lbm_set_allocator(LBM_ALLOC_FN(), LBM_FREE_FN(), None))
+        _allocator = None
+        return
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return alloc(int(nbytes), stream)
+        except Exception:   # becomes LBM_ENOMEM in the calling function
+            return None
+
+    def _release(ptr, stream, ctx):
+        release(ptr, stream)
+
+    cbs = (LBM_ALLOC_FN(_alloc), LBM_FREE_FN(_release))
+    _check(load().lbm_set_allocator(cbs[0], cbs[1], None))
+    _allocator = cbs
 
 
 def lbm_batch_groups(state: int, nbytes: int) -> int:

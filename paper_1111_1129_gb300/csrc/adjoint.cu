@@ -416,10 +416,11 @@ int finish_sums(lbm_adjoint* ad) {
 
 void free_adjoint(lbm_adjoint* ad) {
   if (!ad) return;
-  cudaStreamSynchronize(ad->st ? ad->st->sp->stream : nullptr);
+  const cudaStream_t s = ad->st ? ad->st->sp->stream : nullptr;
+  cudaStreamSynchronize(s);
   for (void* p : {ad->ckpt, ad->seg, ad->lam[0], ad->lam[1], (void*)ad->part,
                   (void*)ad->dalpha, (void*)ad->red_dev})
-    if (p) cudaFree(p);
+    dev_free(p, s, false);
   if (ad->red_host) cudaFreeHost(ad->red_host);
   if (ad->done) cudaEventDestroy(ad->done);
   ad->magic = 0;
@@ -451,13 +452,14 @@ extern "C" int lbm_adjoint_create(const lbm_state* st, int32_t n_steps, int32_t 
   const size_t sbytes = storage_bytes(st->precision) * 19 * n;
   const size_t cbytes = compute_bytes(st->precision) * 19 * n;
   const int nseg = stride > 2 ? stride : 2;
-  bool ok = cudaMalloc(&ad->ckpt, sbytes * ad->n_ckpt) == cudaSuccess &&
-            cudaMalloc(&ad->seg, sbytes * nseg) == cudaSuccess &&
-            cudaMalloc(&ad->lam[0], cbytes) == cudaSuccess &&
-            cudaMalloc(&ad->lam[1], cbytes) == cudaSuccess &&
-            cudaMalloc(&ad->part, sizeof(double) * 4 * st->nblocks) == cudaSuccess &&
-            cudaMalloc(&ad->dalpha, sizeof(double) * n) == cudaSuccess &&
-            cudaMalloc(&ad->red_dev, sizeof(double) * 4) == cudaSuccess &&
+  const cudaStream_t s = st->sp->stream;
+  bool ok = dev_alloc(&ad->ckpt, sbytes * ad->n_ckpt, s, false) == cudaSuccess &&
+            dev_alloc(&ad->seg, sbytes * nseg, s, false) == cudaSuccess &&
+            dev_alloc(&ad->lam[0], cbytes, s, false) == cudaSuccess &&
+            dev_alloc(&ad->lam[1], cbytes, s, false) == cudaSuccess &&
+            dev_alloc(&ad->part, sizeof(double) * 4 * st->nblocks, s, false) == cudaSuccess &&
+            dev_alloc(&ad->dalpha, sizeof(double) * n, s, false) == cudaSuccess &&
+            dev_alloc(&ad->red_dev, sizeof(double) * 4, s, false) == cudaSuccess &&
             cudaMallocHost(&ad->red_host, sizeof(double) * 4) == cudaSuccess &&
             cudaEventCreateWithFlags(&ad->done, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {

@@ -252,9 +252,7 @@ extern "C" int lbm_build_sparse(const uint8_t* flags_dev, const int32_t dims[3],
   for (int k = 0; k < 3; ++k) sp->dims[k] = dims[k];
   sp->ord = ord;
   sp->stream = stream;
-  auto release = [&](void* p) {
-    if (p) cudaFreeAsync(p, stream);
-  };
+  auto release = [&](void* p) { dev_free(p, stream, true); };
   auto cleanup = [&](int status) {
     release(counts);
     release(offsets);
@@ -268,10 +266,10 @@ extern "C" int lbm_build_sparse(const uint8_t* flags_dev, const int32_t dims[3],
     cudaStreamSynchronize(stream);
     return status;
   };
-  if (cudaMallocAsync(&counts, sizeof(uint32_t) * ntiles, stream) != cudaSuccess ||
-      cudaMallocAsync(&offsets, sizeof(int64_t) * ntiles, stream) != cudaSuccess ||
-      cudaMallocAsync(&scal, sizeof(int64_t) * 2, stream) != cudaSuccess ||
-      cudaMallocAsync(&sp->inv, sizeof(int32_t) * box, stream) != cudaSuccess) {
+  if (dev_alloc(&counts, sizeof(uint32_t) * ntiles, stream, true) != cudaSuccess ||
+      dev_alloc(&offsets, sizeof(int64_t) * ntiles, stream, true) != cudaSuccess ||
+      dev_alloc(&scal, sizeof(int64_t) * 2, stream, true) != cudaSuccess ||
+      dev_alloc(&sp->inv, sizeof(int32_t) * box, stream, true) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBM_ENOMEM, "device allocation failed (box %lld cells)", (long long)box));
   }
@@ -293,8 +291,8 @@ extern "C" int lbm_build_sparse(const uint8_t* flags_dev, const int32_t dims[3],
                         (long long)n));
   sp->n = n;
   const size_t nn = (size_t)(n > 0 ? n : 1);
-  if (cudaMallocAsync(&sp->cells, sizeof(int32_t) * nn, stream) != cudaSuccess ||
-      cudaMallocAsync(&sp->adj, sizeof(int32_t) * 18 * nn, stream) != cudaSuccess) {
+  if (dev_alloc(&sp->cells, sizeof(int32_t) * nn, stream, true) != cudaSuccess ||
+      dev_alloc(&sp->adj, sizeof(int32_t) * 18 * nn, stream, true) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBM_ENOMEM, "device allocation failed (%lld fluid cells)", (long long)n));
   }

@@ -423,9 +423,9 @@ void split_groups(const lbm_state* st, int64_t bytes, std::vector<int64_t>& cell
   span_out.push_back(span);
 }
 
-void free_group_tables(Batch* b) {
+void free_group_tables(Batch* b, cudaStream_t stream) {
   for (void* p : {(void*)b->d_chunk_group, (void*)b->d_group_cell0, (void*)b->d_group_span})
-    if (p) cudaFree(p);
+    dev_free(p, stream, false);
   b->d_chunk_group = nullptr;
   b->d_group_cell0 = nullptr;
   b->d_group_span = nullptr;
@@ -452,15 +452,22 @@ int regroup(lbm_state* st, int64_t bytes) {
   for (size_t g = 0; g < G; ++g)
     for (int64_t c = c0[g] / kBatchChunk; c < (c0[g] + span[g]) / kBatchChunk; ++c)
       chunk_group[(size_t)c] = (int32_t)g;
-  bool ok = cudaMalloc(&adj_new, sizeof(int32_t) * 18 * (size_t)(n > 0 ? n : 1)) == cudaSuccess;
+  bool ok = dev_alloc(&adj_new, sizeof(int32_t) * 18 * (size_t)(n > 0 ? n : 1), stream, true) ==
+            cudaSuccess;
   if (ok && G > 1)
-    ok = cudaMalloc(&d_chunk_group, sizeof(int32_t) * chunk_group.size()) == cudaSuccess &&
-         cudaMalloc(&d_c0, sizeof(int64_t) * G) == cudaSuccess &&
-         cudaMalloc(&d_span, sizeof(int64_t) * G) == cudaSuccess;
+    ok = dev_alloc(&d_chunk_group, sizeof(int32_t) * chunk_group.size(), stream, false) ==
+             cudaSuccess &&
+         dev_alloc(&d_c0, sizeof(int64_t) * G, stream, false) == cudaSuccess &&
+         dev_alloc(&d_span, sizeof(int64_t) * G, stream, false) == cudaSuccess;
+  auto release_new = [&]() {
+    dev_free(d_chunk_group, stream, false);
+    dev_free(d_c0, stream, false);
+    dev_free(d_span, stream, false);
+    dev_free(adj_new, stream, true);
+  };
   if (!ok) {
     cudaGetLastError();
-    for (void* p : {(void*)d_chunk_group, (void*)d_c0, (void*)d_span, (void*)adj_new})
-      if (p) cudaFree(p);
+    release_new();
     return fail(LBM_ENOMEM, "allocation for the L2 group layout failed");
   }
   cudaError_t e = cudaSuccess;
@@ -488,8 +495,8 @@ int regroup(lbm_state* st, int64_t bytes) {
   const cudaError_t es = cudaStreamSynchronize(stream);
   if (e == cudaSuccess) e = es;
   if (e != cudaSuccess || rc != LBM_OK) {
-    for (void* p : {(void*)d_chunk_group, (void*)d_c0, (void*)d_span, (void*)adj_new})
-      if (p) cudaFree(p);
+    release_new();
+    cudaStreamSynchronize(stream);
     return rc != LBM_OK ? rc : cuda_fail(e, "L2 group relayout");
   }
   // the cached graph holds the old link array
@@ -498,10 +505,10 @@ int regroup(lbm_state* st, int64_t bytes) {
     b->graph = nullptr;
   }
   lbm_sparse* sp = const_cast<lbm_sparse*>(st->sp);
-  cudaFree(sp->adj);
+  dev_free(sp->adj, stream, true);
   sp->adj = adj_new;
   st->cur ^= 1;
-  free_group_tables(b);
+  free_group_tables(b, stream);
   b->d_chunk_group = d_chunk_group;
   b->d_group_cell0 = d_c0;
   b->d_group_span = d_span;
@@ -571,10 +578,12 @@ void free_batch(lbm_state* st) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->capture) cudaStreamDestroy(b->capture);
+  const cudaStream_t stream = st->sp ? st->sp->stream : nullptr;
+  cudaStreamSynchronize(stream);
   for (void* p : {(void*)b->d_begin, (void*)b->d_count, (void*)b->d_chunk_bed, b->d_force,
                   (void*)b->d_red})
-    if (p) cudaFree(p);
-  free_group_tables(b);
+    dev_free(p, stream, false);
+  free_group_tables(b, stream);
   for (void* p : {b->h_force, (void*)b->h_red})
     if (p) cudaFreeHost(p);
   delete[] b->h_begin;
@@ -615,8 +624,8 @@ extern "C" int lbm_state_create_batched(const lbm_sparse* const* beds, int32_t n
   cat->n = total;
   cat->stream = stream;
   cat->ord.kind = -1;
-  if (cudaMalloc(&cat->adj, sizeof(int32_t) * 18 * (size_t)(total > 0 ? total : 1)) !=
-      cudaSuccess) {
+  if (dev_alloc(&cat->adj, sizeof(int32_t) * 18 * (size_t)(total > 0 ? total : 1), stream,
+                true) != cudaSuccess) {
     cudaGetLastError();
     delete cat;
     return fail(LBM_ENOMEM, "batched adjacency allocation failed");
@@ -663,12 +672,13 @@ extern "C" int lbm_state_create_batched(const lbm_sparse* const* beds, int32_t n
   b->group_cell0.assign(1, 0);
   b->group_span.assign(1, total);
   const size_t fbytes = dispatch_force_bytes(precision);
-  bool ok = cudaMalloc(&b->d_begin, sizeof(int64_t) * n_beds) == cudaSuccess &&
-            cudaMalloc(&b->d_count, sizeof(int32_t) * n_beds) == cudaSuccess &&
-            cudaMalloc(&b->d_chunk_bed, sizeof(int32_t) * chunk_bed.size()) == cudaSuccess &&
-            cudaMalloc(&b->d_force, fbytes * n_beds) == cudaSuccess &&
+  bool ok = dev_alloc(&b->d_begin, sizeof(int64_t) * n_beds, stream, false) == cudaSuccess &&
+            dev_alloc(&b->d_count, sizeof(int32_t) * n_beds, stream, false) == cudaSuccess &&
+            dev_alloc(&b->d_chunk_bed, sizeof(int32_t) * chunk_bed.size(), stream, false) ==
+                cudaSuccess &&
+            dev_alloc(&b->d_force, fbytes * n_beds, stream, false) == cudaSuccess &&
             cudaMallocHost(&b->h_force, fbytes * n_beds) == cudaSuccess &&
-            cudaMalloc(&b->d_red, sizeof(double) * 4 * n_beds) == cudaSuccess &&
+            dev_alloc(&b->d_red, sizeof(double) * 4 * n_beds, stream, false) == cudaSuccess &&
             cudaMallocHost(&b->h_red, sizeof(double) * 4 * n_beds) == cudaSuccess &&
             cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) == cudaSuccess;
   if (!ok) {

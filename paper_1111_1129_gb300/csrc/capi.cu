@@ -1,4 +1,5 @@
-// Error reporting, handle release and version of the C ABI.
+// Error reporting, device memory, handle release and version of the C ABI.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
@@ -9,6 +10,37 @@ namespace lbm {
 
 namespace {
 thread_local std::string g_last_error;
+// The caller's allocator (both null: the library's own) and the number of
+// blocks handed out and not yet released.
+lbm_alloc_fn g_alloc = nullptr;
+lbm_free_fn g_release = nullptr;
+void* g_alloc_ctx = nullptr;
+std::atomic<int64_t> g_live{0};
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t stream, bool ordered) {
+  *p = nullptr;
+  if (g_alloc) {
+    void* q = g_alloc(bytes, (void*)stream, g_alloc_ctx);
+    if (!q) return cudaErrorMemoryAllocation;
+    *p = q;
+  } else {
+    const cudaError_t e = ordered ? cudaMallocAsync(p, bytes, stream) : cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      *p = nullptr;
+      return e;
+    }
+  }
+  ++g_live;
+  return cudaSuccess;
+}
+
+void dev_free(void* p, cudaStream_t stream, bool ordered) {
+  if (!p) return;
+  --g_live;
+  if (g_release) g_release(p, (void*)stream, g_alloc_ctx);
+  else if (ordered) cudaFreeAsync(p, stream);
+  else cudaFree(p);
 }
 
 int fail(int status, const char* fmt, ...) {
@@ -31,8 +63,7 @@ void clear_error() { g_last_error.clear(); }
 void free_sparse(lbm_sparse* sp) {
   if (!sp) return;
   const cudaStream_t s = sp->stream;
-  for (void* p : {(void*)sp->cells, (void*)sp->inv, (void*)sp->adj})
-    if (p) cudaFreeAsync(p, s);
+  for (void* p : {(void*)sp->cells, (void*)sp->inv, (void*)sp->adj}) dev_free(p, s, true);
   cudaStreamSynchronize(s);
   sp->magic = 0;
   delete sp;
@@ -49,5 +80,19 @@ extern "C" void lbm_free(void* handle) {
 }
 
 extern "C" const char* lbm_last_error(void) { return lbm::g_last_error.c_str(); }
+
+extern "C" int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void* ctx) {
+  lbm::clear_error();
+  if ((alloc == nullptr) != (release == nullptr))
+    return lbm::fail(LBM_EINVAL, "give both allocator functions or neither");
+  const int64_t live = lbm::g_live.load();
+  if (live != 0)
+    return lbm::fail(LBM_EINVAL, "%lld device blocks of existing handles are still live",
+                     (long long)live);
+  lbm::g_alloc = alloc;
+  lbm::g_release = release;
+  lbm::g_alloc_ctx = ctx;
+  return LBM_OK;
+}
 
 extern "C" int32_t lbm_abi_version(void) { return 1; }

@@ -19,6 +19,16 @@ constexpr int kWarpsPerBlock = kSweepThreads / 32;
 int fail(int status, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 void clear_error();
+// Device memory of every handle: the caller's allocator when one is set
+// (lbm_set_allocator), else cudaMallocAsync / cudaFreeAsync on `stream`
+// (ordered) or cudaMalloc / cudaFree.  An unordered free expects the work
+// on the block to have finished.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t stream, bool ordered);
+void dev_free(void* p, cudaStream_t stream, bool ordered);
+template <class T>
+cudaError_t dev_alloc(T** p, size_t bytes, cudaStream_t stream, bool ordered) {
+  return dev_alloc(reinterpret_cast<void**>(p), bytes, stream, ordered);
+}
 
 #define LBM_CUDA_TRY(expr)                                         \
   do {                                                             \

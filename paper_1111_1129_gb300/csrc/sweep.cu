@@ -303,7 +303,7 @@ void free_state(lbm_state* st) {
   const cudaStream_t s = st->sp ? st->sp->stream : nullptr;
   cudaStreamSynchronize(s);
   for (void* p : {st->buf[0], st->buf[1], st->alpha, (void*)st->partials, (void*)st->red_dev})
-    if (p) cudaFree(p);
+    dev_free(p, s, false);
   if (st->red_host) cudaFreeHost(st->red_host);
   if (st->done) cudaEventDestroy(st->done);
   if (st->t0) cudaEventDestroy(st->t0);
@@ -345,11 +345,12 @@ extern "C" int lbm_state_create(const lbm_sparse* sp, int32_t precision, int32_t
   // one wave at the 4 resident blocks per SM of the FP32 and 16-bit sweeps
   st->one_wave = st->nblocks <= 4 * (int64_t)sms;
   const size_t bytes = storage_bytes(precision) * 19 * (size_t)(n > 0 ? n : 1);
-  bool ok = cudaMalloc(&st->buf[0], bytes) == cudaSuccess &&
-            cudaMalloc(&st->buf[1], bytes) == cudaSuccess &&
-            cudaMalloc(&st->partials, sizeof(double) * 4 * (kWarpsPerBlock + 1) * st->nblocks) ==
-                cudaSuccess &&
-            cudaMalloc(&st->red_dev, sizeof(double) * 4) == cudaSuccess &&
+  const cudaStream_t stream = sp->stream;
+  bool ok = dev_alloc(&st->buf[0], bytes, stream, false) == cudaSuccess &&
+            dev_alloc(&st->buf[1], bytes, stream, false) == cudaSuccess &&
+            dev_alloc(&st->partials, sizeof(double) * 4 * (kWarpsPerBlock + 1) * st->nblocks,
+                      stream, false) == cudaSuccess &&
+            dev_alloc(&st->red_dev, sizeof(double) * 4, stream, false) == cudaSuccess &&
             cudaMallocHost(&st->red_host, sizeof(double) * 4) == cudaSuccess &&
             cudaEventCreateWithFlags(&st->done, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
@@ -399,15 +400,15 @@ extern "C" int lbm_set_damping(lbm_state* st, const double* alpha_dev) {
   if (!alpha_dev) {
     if (st->alpha) {
       cudaStreamSynchronize(st->sp->stream);
-      cudaFree(st->alpha);
+      dev_free(st->alpha, st->sp->stream, false);
     }
     st->alpha = nullptr;
     return LBM_OK;
   }
   const int64_t n = st->sp->n;
   if (!st->alpha) {
-    if (cudaMalloc(&st->alpha, compute_bytes(st->precision) * (size_t)(n > 0 ? n : 1)) !=
-        cudaSuccess) {
+    if (dev_alloc(&st->alpha, compute_bytes(st->precision) * (size_t)(n > 0 ? n : 1),
+                  st->sp->stream, false) != cudaSuccess) {
       cudaGetLastError();
       st->alpha = nullptr;
       return fail(LBM_ENOMEM, "damping field allocation failed");

@@ -52,6 +52,25 @@ def shifted_scale_exp(dev_bound: float, target_log2: int = 14) -> int:
     return int(max(0, min(40, math.floor(target_log2 - math.log2(dev_bound)))))
 
 
+def use_torch_allocator(enabled: bool = True) -> None:
+    """Take the library's device memory from PyTorch's caching allocator
+    (enabled), so that it shows in torch.cuda.memory_allocated() and is
+    reused with PyTorch's own blocks, or from cudaMalloc (disabled).  Only
+    while no library handle is alive."""
+    if not enabled:
+        capi.lbm_set_allocator(None, None)
+        return
+
+    def alloc(nbytes: int, stream) -> int:
+        return torch.cuda.caching_allocator_alloc(max(nbytes, 1), torch.cuda.current_device(),
+                                                  int(stream or 0))
+
+    def release(ptr: int, stream) -> None:
+        torch.cuda.caching_allocator_delete(ptr)
+
+    capi.lbm_set_allocator(alloc, release)
+
+
 class _DeviceView:
     """Borrowed device buffer exposed through __cuda_array_interface__."""
 

@@ -62,6 +62,14 @@ def test_host_side_validation(lib):
     assert ei.value.status == capi.LBM_EINVAL
 
 
+def test_allocator_needs_both_functions(lib):
+    alloc = capi.LBM_ALLOC_FN(lambda nbytes, stream, ctx: None)
+    assert lib.lbm_set_allocator(alloc, capi.LBM_FREE_FN(), None) == capi.LBM_EINVAL
+    assert "both" in capi.lbm_last_error()
+    # back to the library's own allocator (no handle is alive here)
+    assert lib.lbm_set_allocator(capi.LBM_ALLOC_FN(), capi.LBM_FREE_FN(), None) == capi.LBM_OK
+
+
 def test_missing_library_is_an_error_not_a_fallback(monkeypatch, tmp_path):
     """Without the CUDA library every entry point fails loudly; nothing falls
     back to another implementation."""

@@ -20,6 +20,8 @@ namespace lbm {
 int fail(int status, const char*, ...) { return status; }
 int cuda_fail(cudaError_t, const char*) { return LBM_ECUDA; }
 void clear_error() {}
+cudaError_t dev_alloc(void**, size_t, cudaStream_t, bool) { return cudaErrorMemoryAllocation; }
+void dev_free(void*, cudaStream_t, bool) {}
 }
 #include "../csrc/assembly.cu"
 int main(int argc, char** argv) {
