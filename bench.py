@@ -31,6 +31,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -112,7 +113,11 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to $LBM_CLOCKS_DIR (default: a temporary folder);
+        # the JSON line carries their summary
+        out_dir = os.environ.get("LBM_CLOCKS_DIR") or os.path.join(tempfile.gettempdir(),
+                                                                   "lbm_clocks")
+        self.path = os.path.join(out_dir, f"clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
