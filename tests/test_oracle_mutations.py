@@ -1,8 +1,8 @@
 """The oracle's pins catch plausible mistakes.  Each case plants one mistake
 in a copy of oracle/lbm_oracle.c (a dropped term, a swapped rate, a wrong
 weight, sign, coefficient, slot or key bit), builds it on the side, and
-runs every pin of tests/test_oracle_pins.py against it: at least one pin
-must fail.  Every mistake keeps all memory accesses in bounds.  The oracle
+runs every pin of tests/test_oracle_pins.py (and the sparse-stepper pin of
+tests/test_partition.py) against it: at least one pin must fail.  Every mistake keeps all memory accesses in bounds.  The oracle
 itself is not modified."""
 import itertools
 import os
@@ -62,15 +62,24 @@ MISTAKES = [
     ("direct dJ/dF term dropped",
      "dJdF[axis] += 0.5 * s / (double)nf;",
      "dJdF[axis] += 0.0 * s / (double)nf;"),
+    ("sparse stepper reads the rest value from the wrong row",
+     "g[0] = f_src[i];",
+     "g[0] = f_src[n + i];"),
+    ("sparse stepper stores the pulled values uncollided",
+     "for (int q = 0; q < 19; ++q) f_dst[(int64_t)q * n + i] = fo[q];",
+     "for (int q = 0; q < 19; ++q) f_dst[(int64_t)q * n + i] = g[q];"),
 ]
 
 
 def _pin_calls():
-    """Every pin of test_oracle_pins.py, its parametrisations expanded."""
+    """Every pin of test_oracle_pins.py, its parametrisations expanded, and
+    the sparse-stepper pin of test_partition.py."""
     from tests import test_oracle_pins as pins
+    from tests import test_partition as part
+    fns = [(name, getattr(pins, name)) for name in sorted(dir(pins))]
+    fns.append(("test_sparse_step_matches_dense_pull", part.test_sparse_step_matches_dense_pull))
     calls = []
-    for name in sorted(dir(pins)):
-        fn = getattr(pins, name)
+    for name, fn in fns:
         if not (name.startswith("test_") and callable(fn)):
             continue
         grids = []
