@@ -254,10 +254,16 @@ void lbm_set_timeout(double timeout_s);
  *              of this step's collision (flux = sum u_axis / N).
  *   stream:    cudaStream_t the work is queued on (asynchronous).
  * Its only scratch, the FP64 block partial sums (at most 65,536 blocks of
- * 256 cells), lives in a fixed 2 MiB static device array that every GPU
- * loading this library holds until the process exits.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) with
- * the device current; make that first call before any stream capture.
+ * 256 cells), lives in a fixed 2 MiB static device array, part of the
+ * library's compiled sweep code.  Under CUDA's lazy module loading (the
+ * default) the driver loads that code on a device, and reserves the array
+ * there, when it is first used on that device -- at the latest by this
+ * entry point's first call there -- not when the library is loaded; from
+ * then on the device holds the array until the process exits.  The first
+ * call on a device also looks up the array's device address
+ * (cudaGetSymbolAddress) with the device current.  So make the first call
+ * on each device before the caller takes all of that device's memory, and
+ * before any stream capture; later calls need neither.
  * Every call shares the array and it keeps the last call's contents; each
  * call overwrites the entries it reads, so nothing needs clearing, but two
  * calls that overlap on the same GPU (for example on two streams) race on

@@ -1,12 +1,16 @@
 """Virtual ranks on one GPU: the list cut into P chunks, ghosts filled by
 lbm_halo_gather from the owners' arrays before every step, each chunk
-stepped on its own local adjacency.  The result must equal the unsplit
-lbm_step bit for bit (same per-cell arithmetic), and the per-chunk sums
-must add up to the unsplit mass and flux."""
+stepped on its own local adjacency (Sec. 2 and Fig. 1c: equal chunks of
+the 1-D list, remote links exchanged).  The gathered result must equal the
+FP64 oracle's run of the unsplit bed within the FP64 tolerance, and the
+unsplit lbm_step bit for bit (same per-cell arithmetic); the per-chunk
+sums must add up to the oracle's and the unsplit mass and flux."""
 import numpy as np
 import pytest
 import torch
 
+import fp64_measures
+import oracle
 from paper_1111_1129_gb300 import LBMState, SparseLattice, build, capi, inputs, omega_minus
 from paper_1111_1129_gb300.partition import plan
 
@@ -60,8 +64,20 @@ def test_virtual_ranks_equal_the_unsplit_run(p, ordering):
         cur ^= 1
     got = torch.cat([bufs[k][cur][:19 * pl.count].view(19, pl.count)
                      for k, pl in enumerate(plans)], dim=1)
-    assert torch.equal(got, ref_f)
+    # against the oracle's dense run of the unsplit bed
+    order = {"lex": oracle.ORDER_LEX, "blocked": oracle.ORDER_BLOCKED,
+             "morton1": oracle.ORDER_MORTON1}[ordering]
+    cells, _, adj_ref = oracle.build_sparse(bed.flags, order, (8, 8, 8), bed.periodic)
+    np.testing.assert_array_equal(lat.cells().cpu().numpy(), cells)
+    np.testing.assert_array_equal(adj, adj_ref)
+    f_or, obs, _, _ = oracle.run(bed.flags, bed.periodic, WP, WM, F, steps)
+    m = fp64_measures.check(got.cpu().numpy(), oracle.to_sparse(f_or, cells), steps,
+                            label=f"virtual ranks p={p} {ordering}")
     tot = sums.sum(dim=0).cpu().numpy()
+    assert abs(tot[0] - obs[-1, 0]) <= 1e-12 * obs[-1, 0]
+    assert abs(tot[3] / n - obs[-1, 3] / n) <= 11 * m["bound_abs_df"] + 2.0 ** -61
+    # and the unsplit GPU run, bit for bit
+    assert torch.equal(got, ref_f)
     assert abs(tot[0] - ref_mass) <= 1e-12 * ref_mass
     assert abs(tot[3] / n - ref_flux) <= 1e-12 * abs(ref_flux)
     ref.close()

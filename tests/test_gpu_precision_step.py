@@ -27,6 +27,7 @@ import torch
 import oracle
 from paper_1111_1129_gb300 import LBMState, SparseLattice, build, capi, inputs, omega_minus
 from paper_1111_1129_gb300 import shifted_scale_exp
+from storage_units import W, codes_equal_fraction, one_step_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -34,8 +35,6 @@ WP = 1.0 / 0.8
 WM = omega_minus(WP)
 F = (3e-6, -2e-6, 5e-6)
 DEV = 1e-4
-W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
-EPS32 = 2.0 ** -24
 
 
 @pytest.fixture(scope="module")
@@ -48,29 +47,6 @@ def lattice():
     np.testing.assert_array_equal(lat.cells().cpu().numpy(), cells)
     yield lat, adj, len(cells)
     lat.close()
-
-
-def _ulp_f16(v):
-    """Spacing of FP16 at |v| (v already scaled), from numpy's float16."""
-    return np.spacing(np.abs(v).astype(np.float16)).astype(np.float64)
-
-
-def _ulp_bf16(v):
-    """Spacing of BF16 (8-bit significand, FP32 exponent range) at |v|."""
-    a = np.abs(v)
-    e = np.floor(np.log2(np.where(a > 0, a, 2.0 ** -126)))
-    return 2.0 ** (np.maximum(e, -126) - 7)
-
-
-def _ulp_f32(v):
-    return np.spacing(np.abs(v).astype(np.float32)).astype(np.float64)
-
-
-def _rn_bf16(v):
-    """Round FP64 to BF16 (via FP32, nearest even), returned as FP64."""
-    u = np.asarray(v, np.float64).astype(np.float32).view(np.uint32).astype(np.uint64)
-    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
-    return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 @pytest.mark.parametrize("damped", [False, True])
@@ -92,19 +68,8 @@ def test_one_step_within_one_storage_unit(lattice, precision, damped):
     st.close()
     f_ref = oracle.sparse_step(f_rep, adj, n, F, WP, WM, alpha).reshape(19, n)
 
-    dev_rep = f_rep - W[:, None]
-    big = 19.0 * np.abs(dev_rep).max()         # bound on any intermediate deviation sum
     err = np.abs(f_gpu - f_ref)
-    scale = 2.0 ** k
-    d_ref = (f_ref - W[:, None]) * scale        # exact: the subtraction cancels w's bits
-    if precision == "f16s":
-        tol = _ulp_f16(d_ref) / scale + 64 * EPS32 * big
-    elif precision == "bf16s":
-        tol = _ulp_bf16(d_ref) / scale + 64 * EPS32 * big
-    elif precision == "f32s":   # measured: 0.14 of this bound
-        tol = _ulp_f32(f_ref - W[:, None]) + 4 * EPS32 * big
-    else:   # FP32 of f itself: the arithmetic works on values up to rho ~ 1 (measured 0.27)
-        tol = _ulp_f32(f_ref) + 6 * EPS32
+    tol = one_step_tolerance(precision, f_ref, float(np.abs(f_rep - W[:, None]).max()), k)
     worst = float((err / tol).max())
     print(f"{precision} damped={damped} n={n} k={k} max|err|={err.max():.3e} "
           f"max err/tol={worst:.3f}")
@@ -112,9 +77,6 @@ def test_one_step_within_one_storage_unit(lattice, precision, damped):
     assert worst <= 1.0, (precision, damped, worst)
 
     if precision in ("f16s", "bf16s"):
-        code_gpu = (f_gpu - W[:, None]) * scale
-        code_ref = (d_ref.astype(np.float16).astype(np.float64) if precision == "f16s"
-                    else _rn_bf16(d_ref))
-        same = float(np.mean(code_gpu == code_ref))
+        same = codes_equal_fraction(precision, f_gpu, f_ref, k)
         print(f"{precision} damped={damped}: codes equal to the rounded FP64 result: {same:.5f}")
         assert same >= 0.99, same

@@ -3,9 +3,11 @@ cannot allocate device memory -- for example an application that owns all
 of the GPU's memory and lends this library only the arrays it works on.
 
 Its output must equal what the allocating entry points produce (lbm_step on
-an FP64 state, then lbm_state_get_pdfs and lbm_reduce_flux) within the FP64
-tolerance of the other tests, on two calls in a row.  The file is named so
-that pytest collects it last.
+an FP64 state, then lbm_state_get_pdfs and lbm_reduce_flux along each axis)
+within the FP64 tolerance of the other tests, on two calls in a row.  After
+a first call on the device (which loads the library's code there and with
+it the static scratch), further calls must leave the device's free memory
+unchanged.  The file is named so that pytest collects it last.
 """
 import numpy as np
 import pytest
@@ -43,20 +45,32 @@ def test_noalloc_step_matches_the_allocating_entry_points(damped):
     F = (1e-5, -2e-6, 3e-5)
     fa = f0.clone()
     fb = torch.empty_like(fa)
+    warm = torch.empty_like(fa)
     sums = torch.empty(4, dtype=torch.float64, device="cuda")
     stream = int(torch.cuda.current_stream().cuda_stream)
+    a_ptr = alpha.data_ptr() if damped else None
+    # first call on the device: loads the code and its static scratch
+    capi.lbm_step_f64_noalloc(fa.data_ptr(), warm.data_ptr(), adj_ptr, n, WP, WM, F, a_ptr,
+                              sums.data_ptr(), stream)
+    torch.cuda.synchronize()
     for _ in range(2):
         st.step(1, WP, WM, F)
-        mass, flux = st.reduce_flux(2)
+        ref_sums = [st.reduce_flux(axis) for axis in range(3)]
         ref = st.get_pdfs()
-        capi.lbm_step_f64_noalloc(fa.data_ptr(), fb.data_ptr(), adj_ptr, n, WP, WM, F,
-                                  alpha.data_ptr() if damped else None, sums.data_ptr(), stream)
         torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        capi.lbm_step_f64_noalloc(fa.data_ptr(), fb.data_ptr(), adj_ptr, n, WP, WM, F, a_ptr,
+                                  sums.data_ptr(), stream)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
         err = (fb - ref).abs().max().item() / ref.abs().max().item()
         assert err <= TOL, err
         s = sums.cpu().numpy()
+        mass = ref_sums[0][0]
         assert abs(s[0] - mass) <= TOL * abs(mass)
-        assert abs(s[3] / n - flux) <= TOL * abs(flux)
+        for axis in range(3):
+            flux = ref_sums[axis][1]
+            assert abs(s[1 + axis] / n - flux) <= TOL * max(abs(flux), 1e-300), (axis, s, flux)
         fa, fb = fb, fa
     st.close()
     lat.close()
@@ -69,3 +83,12 @@ def test_noalloc_step_rejects_sizes_beyond_its_scratch():
                                   sums.data_ptr(), 0)
     assert ei.value.status == capi.LBM_EINVAL
     assert "16777216" in str(ei.value)
+
+
+def test_noalloc_step_on_an_empty_list_gives_zero_sums():
+    sums = torch.full((4,), 7.0, dtype=torch.float64, device="cuda")
+    stream = int(torch.cuda.current_stream().cuda_stream)
+    capi.lbm_step_f64_noalloc(0, 0, 0, 0, WP, WM, (0.0, 0.0, 1e-6), None, sums.data_ptr(),
+                              stream)
+    torch.cuda.synchronize()
+    assert sums.tolist() == [0.0, 0.0, 0.0, 0.0]
