@@ -115,6 +115,11 @@ int launch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const dou
   const Coef<C> k = make_coef<C>(wp, wm, F, st->scale_exp);
   const unsigned grid = (unsigned)st->nblocks;
   const C* alpha = (const C*)st->alpha;
+  // the 16-bit forms take two adjacent cells per thread in their plain steps
+  // on grids of more than one wave
+  constexpr bool kPairForm = LBM_PAIR_SWEEP && (PREC == LBM_F16S || PREC == LBM_BF16S);
+  constexpr int64_t kPairCells = 2 * (int64_t)kPairThreads;
+  const unsigned grid_pair = (unsigned)((n + kPairCells - 1) / kPairCells);
   for (int32_t t = 0; t < n_steps; ++t) {
     const S* src = (const S*)st->buf[st->cur];
     S* dst = (S*)st->buf[st->cur ^ 1];
@@ -129,6 +134,14 @@ int launch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const dou
       const bool chained = kMemoryBound && t > 0;
       // a grid of one wave loads its links before the wait (sweep_kernel)
       const bool links_first = kMemoryBound && st->one_wave && !last;
+      if constexpr (kPairForm) {
+        if (!last && !st->one_wave) {
+          if (alpha) LBM_CUDA_TRY(launch_chained(sweep_pair_kernel<PREC, true>, grid_pair, (unsigned)kPairThreads, stream, chained, src, dst, adj, n, k, alpha));
+          else LBM_CUDA_TRY(launch_chained(sweep_pair_kernel<PREC, false>, grid_pair, (unsigned)kPairThreads, stream, chained, src, dst, adj, n, k, alpha));
+          st->cur ^= 1;
+          continue;
+        }
+      }
       if (alpha) {
         if (last) LBM_CUDA_TRY(launch_sweep(sweep_kernel<PREC, true, kWarpSums>, grid, stream, chained, src, dst, adj, n, k, alpha, st->partials));
         else if (links_first) LBM_CUDA_TRY(launch_sweep(sweep_kernel<PREC, true, kNoReduce, kMemoryBound>, grid, stream, chained, src, dst, adj, n, k, alpha, st->partials));
@@ -538,8 +551,10 @@ extern "C" void lbm_set_timeout(double timeout_s) {
 // device-wide synchronisation and latency of a cudaMalloc.  This entry point
 // takes every input and output from the caller and keeps its one piece of
 // scratch -- the FP64 block partial sums of the reduction -- in a fixed
-// static device array, present on every GPU that loads the library until
-// the process exits.
+// static device array.  Under lazy module loading the driver reserves the
+// array on a device when this file's device code is first used there (at
+// the latest by the first call of this entry point on that device); the
+// device then holds it until the process exits.
 namespace lbm {
 namespace {
 

@@ -1,0 +1,60 @@
+"""The 16-bit sweep that updates two adjacent cells per thread.
+
+Its plain steps run on grids of more than one wave, and the reducing last
+step of a call runs the one-cell kernel, so a run taken in one call must
+equal the same steps taken one call each bit for bit (same per-cell
+arithmetic).  The cases cover both parities of the list length N (an odd
+N leaves one cell alone at the end of the list),
+damping, and an order in which neighbouring cells rarely pull from
+neighbouring slots (Morton, 2-bit) as well as the lexicographic order in
+which they mostly do.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1111_1129_gb300 import LBMState, SparseLattice, build, capi, inputs, omega_minus
+
+pytestmark = pytest.mark.gpu
+
+WP = 1.0 / 0.8
+WM = omega_minus(WP)
+F = (2e-6, -1e-6, 1e-5)
+
+
+@pytest.fixture(scope="module", params=["even", "odd"])
+def flags(request):
+    build.build()
+    capi.load()
+    bed = inputs.packed_bed((96, 80, 72), 2, 70.0, 5.0, 0.45, 3)
+    f = bed.flags.copy()
+    want = 0 if request.param == "even" else 1
+    if int((f == 0).sum()) % 2 != want:
+        z, y, x = np.argwhere(f == 0)[len(np.argwhere(f == 0)) // 2]
+        f[z, y, x] = 1
+    assert int((f == 0).sum()) % 2 == want
+    return f, bed.periodic
+
+
+@pytest.mark.parametrize("ordering", ["lex", "morton2"])
+@pytest.mark.parametrize("damped", [False, True])
+@pytest.mark.parametrize("precision", ["f16s", "bf16s"])
+def test_pair_steps_equal_single_cell_steps(flags, precision, damped, ordering):
+    f, periodic = flags
+    lat = SparseLattice(torch.from_numpy(f).cuda(), ordering, (8, 8, 8), periodic)
+    assert lat.n > 4 * 152 * 256          # more than one wave: the paired kernel runs
+    alpha = None
+    if damped:
+        alpha = torch.from_numpy(np.random.default_rng(5).uniform(0.0, 0.05, lat.n))
+    out = []
+    for calls in ([9], [1] * 9):
+        st = LBMState(lat, precision, 22)
+        if damped:
+            st.set_damping(alpha)
+        for k in calls:
+            st.step(k, WP, WM, F)
+        out.append((st.get_pdfs(), st.reduce_flux(2)))
+        st.close()
+    assert torch.equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+    lat.close()
