@@ -3,11 +3,11 @@
 Workload: the 1024x256x256 packed bed (tube of diameter 250 along x,
 spheres of radius 8 by seeded random sequential addition, periodic in x,
 ~33 M fluid cells), body force 1e-6 along x, omega+ = 1/0.8, Lambda = 3/16,
-rest initial state, FP64 PDFs, 8^3-blocked lexicographic order.  The
-default form is f64x: FP64 storage with the update computed in exact 64-bit
-fixed point (results equal IEEE FP64 to round-off); --precision f64 times
-the IEEE-FP64-arithmetic kernel, which GB300's FP64 rate caps near 4.3
-GLUP/s.
+rest initial state, FP64 PDFs, lexicographic order (--ordering picks
+another).  The default form is f64x: FP64 storage with the update computed
+in exact 64-bit fixed point (results equal IEEE FP64 to round-off);
+--precision f64 times the IEEE-FP64-arithmetic kernel, which GB300's FP64
+rate caps near 4.3 GLUP/s.
 
 One "step" is one time step of the hot path: pull through the adjacency
 list, TRT collision, streaming store (one kernel launch per step), with the
@@ -15,10 +15,12 @@ FP64 mass/flux reduction fused into the last step and finished by
 lbm_reduce_flux.  MFLUP/s counts fluid cells only (Sec. 7).
 
 The JSON line carries: value (device-resident inputs), e2e (the same metric
-through the C ABI from host flags to a host result, copies included),
-roofline of the sweep kernel, the CPU oracle timed on a bounded sample, the
-SM clocks sampled during the timed region, and extra measurements
-(orderings, storage forms) each labelled with its own step count.
+through the C ABI from pinned host flags to a host result, the copies inside
+the library's calls), roofline of the sweep kernel, the CPU oracle timed on
+a bounded sample, the SM clocks sampled during the timed region, the rates
+of the IEEE-FP64 and FP16-shifted forms beside the headline with their
+ratios, and extra measurements (orderings, storage forms) each labelled
+with its own step count.
 
 --impl reference times the CPU oracle instead (the only reference this
 method has) on a bounded sample of the same workload.
@@ -45,13 +47,13 @@ BYTES_PER_LUP = {"f64": 19 * 8 * 2 + 18 * 4, "f64x": 19 * 8 * 2 + 18 * 4,
                  "f32s": 19 * 4 * 2 + 18 * 4, "f16s": 19 * 2 * 2 + 18 * 4,
                  "bf16s": 19 * 2 * 2 + 18 * 4}
 # DRAM bytes (read + write) per fluid update of one sweep launch, measured by
-# ncu per (workload, form, ordering) on the full-size bed in one 1-pass
-# capture (profiles/sweep_f64x_f32s_f16s_bed1024x256x256_dram.md).  The
-# roofline's `traffic` multiplies them by the benchmark's cells.  Drop an
-# entry when its kernel changes.
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum of one launch, after
+# three warm-up steps) per (workload, form, ordering).  The roofline's
+# `traffic` multiplies them by the benchmark's cells.  Drop an entry when its
+# kernel changes.
 MEASURED_DRAM_BYTES_PER_LUP = {
     ("large", "f64x", "lex"): 379.1, ("large", "f32s", "lex"): 223.3,
-    ("large", "f16s", "lex"): 147.4,
+    ("large", "f16s", "lex"): 147.3,
 }
 STORAGE = {"f64": "f64", "f64x": "f64", "f32": "f32", "f32s": "f32 (f - w)",
            "f16s": "f16 ((f - w) 2^k)", "bf16s": "bf16 ((f - w) 2^k)"}
@@ -59,9 +61,10 @@ ARITHMETIC = {"f64": "f64", "f64x": "int64", "f32": "f32", "f32s": "f32", "f16s"
               "bf16s": "f32"}
 ARITHMETIC_NOTE = {
     "f64": "IEEE FP64",
-    "f64x": "exact 64-bit fixed point on f - w (unit 2^-58); results agree with IEEE FP64 to "
-            "round-off (parity 1e-12 vs the oracle) and conserve the stored mass exactly; "
-            "cells outside the fast range use IEEE FP64",
+    "f64x": "FP64 storage; update exact to FP64 round-off (int64 fixed point on f - w, unit "
+            "2^-58): results agree with IEEE FP64 to round-off (parity 1e-12 of max|f| vs the "
+            "oracle) and conserve the stored mass exactly; cells outside the fast range use "
+            "IEEE FP64",
     "f32": "FP32", "f32s": "FP32", "f16s": "FP32", "bf16s": "FP32"}
 # name: (label, input generator, flow axis, tube radius).  The body force,
 # 1e-6, points along the tube.
@@ -293,11 +296,12 @@ def run_ours(args):
     launch_ms = ms / args.steps
     st.close()
 
-    # ---- e2e: host flags -> C ABI -> host result, copies inside ----------
+    # ---- e2e: pinned host flags -> C ABI -> host result -------------------
+    # lbm_build_sparse copies the host flags to the device itself, and
+    # lbm_reduce_flux returns the sums in host memory
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    flags_dev = flags_host.to("cuda", non_blocking=True)
-    h_lat = capi.lbm_build_sparse(flags_dev.data_ptr(), bed.dims,
+    h_lat = capi.lbm_build_sparse(flags_host.data_ptr(), bed.dims,
                                   capi.make_ordering(lbm_mod.ORDERINGS[args.ordering],
                                                      (8, 8, 8), bed.periodic),
                                   int(stream.cuda_stream))
@@ -317,6 +321,20 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_extra:
         extra = _extras(lat, bed, wm, args, force, k16)
+    forms = None
+    if extra:
+        # the headline beside the IEEE-FP64 and FP16-shifted rates (extra's
+        # shorter runs) and the ratios of the FP16-shifted form to each
+        rate = dict(extra["by_storage_mflups"])
+        rate[args.precision] = value
+        forms = {f"{p}_mflups": rate[p] for p in ("f64x", "f64", "f32s", "f16s") if p in rate}
+        if "f16s" in rate:
+            for p in ("f64x", "f64"):
+                if p in rate:
+                    forms[f"f16s_over_{p}"] = rate["f16s"] / rate[p]
+        forms["note"] = ("f64x: FP64 storage, int64 fixed-point update; f64: IEEE FP64 "
+                         "arithmetic; headline form from the timed run, the others from "
+                         f"{args.extra_steps}-step runs")
     if rank == 0 and world == 1 and not args.no_cpu:
         mflups, steps_c, n_c, cores, dt, label = _oracle_sample(bed, args.cpu_seconds, force)
         cpu = {"value": mflups, "unit": "MFLUP/s", "cores": cores, "kind": "oracle",
@@ -349,7 +367,9 @@ def run_ours(args):
                                  in MEASURED_DRAM_BYTES_PER_LUP else None),
                      "bytes_per_lup": bpl, "peak_kind": peak_kind,
                      "kernel": "sweep_fx_kernel" if args.precision == "f64x"
-                     else f"sweep_kernel<{args.precision}>"},
+                     else (f"sweep_pair_kernel<{args.precision}>"
+                           if args.precision in ("f16s", "bf16s") else
+                           f"sweep_kernel<{args.precision}>")},
         "e2e": {"value": e2e_value, "unit": "MFLUP/s",
                 "h2d_bytes_per_step": (bed.flags.nbytes + 24) / args.steps,
                 "d2h_bytes_per_step": 32 / args.steps},
@@ -357,6 +377,8 @@ def run_ours(args):
         "clocks": clocks.summary(),
         "result": {"mass": mass, "flux": flux, "e2e_flux": e2e_flux},
     }
+    if forms is not None:
+        line["forms"] = forms
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if extra:
@@ -410,24 +432,39 @@ def _extras(lat, bed, wm, args, force, k16):
 
 
 def run_precision_study(args):
-    """Storage forms against the FP64 GPU path on the 256x128x128 bed at
-    steady state (the FP64 path itself is held to the oracle within 1e-12 by
-    the parity tests): velocity-field L2 error, permeability (mean axial
-    velocity) error, mass drift and MFLUP/s.  Prints one JSON line."""
+    """Storage forms against the FP64 oracle on the 256x128x128 bed at
+    steady state: velocity-field L2 error, permeability (mean axial
+    velocity) error, mass drift and MFLUP/s.  The reference is the oracle's
+    own 20,000-step run of this bed, stored by
+    tests/golden/make_medium_bed_reference.py (velocity field in FP32, sums
+    in FP64); the GPU FP64 forms are listed against it too.  Prints one JSON
+    line."""
+    import hashlib
+
     import numpy as np
     import torch
 
     from paper_1111_1129_gb300 import (LBMState, SparseLattice, capi, deviation_bound, inputs,
                                        omega_minus, shifted_scale_exp)
 
+    ref_path = os.path.join(ROOT, "tests", "golden", "medium_bed_u_fp64_oracle.npz")
+    if not os.path.exists(ref_path):
+        raise SystemExit(f"{ref_path} is missing: run tests/golden/make_medium_bed_reference.py")
+    with np.load(ref_path) as z:
+        ref = {k: z[k] for k in z.files}
+    if args.study_steps != int(ref["steps"]):
+        raise SystemExit(f"the oracle reference is for {int(ref['steps'])} steps")
+    ref_u = ref["u"].astype(np.float64)
     capi.load()
     wm = omega_minus(WP)
     bed = inputs.bed_medium(0)
-    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), args.ordering, (8, 8, 8),
-                        bed.periodic)
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "lex", (8, 8, 8), bed.periodic)
+    cells = lat.cells().cpu().numpy().astype(np.int32)
+    if hashlib.sha256(cells.tobytes()).hexdigest() != str(ref["cells_sha256"]):
+        raise SystemExit("the stored oracle field is for another cell list")
+    flux_ref = float(ref["sums"][1]) / lat.n
     k16 = shifted_scale_exp(deviation_bound(FORCE[0], 61.0, WP))
     rows = {}
-    ref_u = ref_flux = None
     for prec in ("f64", "f64x", "f32s", "f16s", "f32", "bf16s"):
         st = LBMState(lat, prec, k16)
         torch.cuda.synchronize()
@@ -440,19 +477,21 @@ def run_precision_study(args):
         _, u = st.moments()
         u = u.cpu().numpy()
         st.close()
-        if ref_u is None:
-            ref_u, ref_flux = u, flux
         rows[prec] = {
             "mflups": lat.n * args.study_steps / (ms * 1e-3) / 1e6,
-            "u_l2_rel_vs_f64": float(np.linalg.norm(u - ref_u) / np.linalg.norm(ref_u)),
-            "permeability_rel_vs_f64": abs(flux - ref_flux) / abs(ref_flux),
+            "u_l2_rel": float(np.linalg.norm(u - ref_u) / ref["u_norm"]),
+            "permeability_rel": abs(flux - flux_ref) / abs(flux_ref),
             "mass_drift_rel": abs(mass - lat.n) / lat.n,
             "finite": bool(np.isfinite(u).all()),
         }
     line = {"study": "storage precision at steady state",
             "workload": WORKLOADS["medium"][0], "fluid_cells": lat.n,
-            "steps": args.study_steps, "force": list(FORCE), "ordering": args.ordering,
-            "scale_exp_16bit": k16, "reference": "f64 GPU path", "forms": rows}
+            "steps": args.study_steps, "force": list(FORCE), "ordering": "lex",
+            "scale_exp_16bit": k16,
+            "reference": "FP64 oracle (dense full-array solver), same bed and steps; stored "
+                         "velocity field in FP32 (L2 errors below ~3e-8 are its resolution), "
+                         "sums in FP64",
+            "forms": rows}
     lat.close()
     print(json.dumps(line), flush=True)
     return 0
@@ -510,6 +549,42 @@ def run_adjoint_study(args):
     lat.close()
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _l2_copy_ceiling(frac: float = 0.6, copies: int = 50, seconds: float = 1.5):
+    """Copy bandwidth of data resident in L2: two FP32 buffers holding
+    `frac` of the L2 together, copied back and forth `copies` times in one
+    CUDA graph, best of the replays of `seconds`, each timed with CUDA
+    events on the launching stream (the clocks are sampled meanwhile).
+    Counts read + write bytes.  Returns (GB/s, bytes per buffer, clocks)."""
+    import torch
+
+    l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+    nbytes = int(frac * l2 / 2) // 4096 * 4096
+    a = torch.ones(nbytes // 4, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            b.copy_(a)
+            a.copy_(b)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for i in range(copies):
+                (b if i % 2 == 0 else a).copy_(a if i % 2 == 0 else b)
+        best = None
+        with ClockSampler(torch.cuda.current_device()) as clocks:
+            t_end = time.perf_counter() + seconds
+            while time.perf_counter() < t_end:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                g.replay()
+                e1.record(s)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+    s.synchronize()
+    return 2 * nbytes * copies / (best * 1e-3) / 1e9, nbytes, clocks.summary()
 
 
 def run_batch_study(args):
@@ -574,7 +649,20 @@ def run_batch_study(args):
         st.close()
     for l in lats:
         l.close()
+    # L2 groups stream from L2: their roofline is an L2 copy ceiling
+    # measured here; 224 algorithmic bytes per update (19 FP32 loads, 19 FP32
+    # stores, 18 int32 links), plus the per-block bed-table reads (chunk's
+    # bed, begin, count, force: 52 bytes per block of block x cells/thread)
+    l2_gbs, l2_buf, l2_clocks = _l2_copy_ceiling()
+    bpl = 224 + 52 / (block * cpt)
+    achieved = bpl * n_fluid * K / (out["batched_l2_groups"]["ms"] * 1e-3) / 1e9
+    roofline = {"bound": "l2", "achieved": achieved, "peak": l2_gbs, "unit": "GB/s",
+                "frac": achieved / l2_gbs, "bytes_per_lup": bpl,
+                "peak_kind": f"measured here: L2-resident copy, 2 x {l2_buf / 1e6:.1f} MB "
+                             "FP32 buffers, 50 copies per CUDA graph, best replay of 1.5 s",
+                "peak_clocks": l2_clocks, "kernel": "batch_sweep_kernel<f32s> (L2 groups)"}
     line = {"study": "batched beds", "n_beds": 256, "fluid_cells": n_fluid, "steps": K,
+            "roofline": roofline,
             "ordering": args.ordering, "precision": "f32s", "tuned": {"block": block, "cells_per_thread": cpt,
                                            "candidate_ms_block_major": cand},
             **out, "speedup_vs_separate": out["batched_l2_groups"]["mflups"] /
@@ -673,7 +761,7 @@ def main():
     ap.add_argument("--ordering", default="lex", choices=["lex", "blocked", "morton1",
                                                                "morton2", "hilbert"])
     ap.add_argument("--precision", default="f64x", choices=list(BYTES_PER_LUP))
-    ap.add_argument("--extra-steps", type=int, default=50)
+    ap.add_argument("--extra-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

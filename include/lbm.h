@@ -113,9 +113,11 @@ int lbm_ordering_keys(const int32_t dims[3], lbm_ordering ord, uint64_t* keys_de
 
 /*
  * Build the sparse representation of a voxelised domain (Sec. 2-3).
- * flags_dev: device uint8[nx*ny*nz], box layout, 0 fluid / 1 solid, read
- *            only, owned by the caller, must stay valid until this call
- *            returns.
+ * flags:     uint8[nx*ny*nz], box layout, 0 fluid / 1 solid, read only,
+ *            owned by the caller, must stay valid until this call returns;
+ *            device memory, or host memory (pinned or pageable), which is
+ *            first copied on `stream` into a device buffer that the call
+ *            allocates and releases.
  * dims:      host int32[3], each >= 1, nx*ny*nz < 2^31 (the paper's solver
  *            has the same bound on the bounding box, Sec. 7 end).
  * ord:       numbering scheme and periodic axes.
@@ -125,10 +127,10 @@ int lbm_ordering_keys(const int32_t dims[3], lbm_ordering ord, uint64_t* keys_de
  *            fluid cells ranked by key), inv[nx*ny*nz] (n, or -1 for solid)
  *            and adj[18*N] (layout above).
  * The call synchronises `stream` (to learn N, and again before returning,
- * so flags_dev may be released afterwards).  Errors: LBM_EINVAL,
+ * so the flags may be released afterwards).  Errors: LBM_EINVAL,
  * LBM_EFLAGS, LBM_EOVERFLOW (19*N >= 2^31), LBM_ENOMEM, LBM_ECUDA.
  */
-int lbm_build_sparse(const uint8_t* flags_dev, const int32_t dims[3], lbm_ordering ord,
+int lbm_build_sparse(const uint8_t* flags, const int32_t dims[3], lbm_ordering ord,
                      void* stream, lbm_sparse** out);
 
 /*

@@ -29,7 +29,7 @@
  *     carry ghost slots.
  *
  * The paper names TRT [Ginzburg] but does not print its equations.  The
- * readings used here (see the design notes of the repository):
+ * readings used here, which the GPU path shares:
  *   rho = sum_q g_q,  j = sum_q c_q g_q,  rho0 = 1 (incompressible form),
  *   u   = (j + F/2) / (1 + alpha/2)          (implicit Brinkman, half force),
  *   F_n = F - alpha u                        (Brinkman-damped body force),

@@ -119,9 +119,9 @@ def lbm_ordering_keys(dims, ordering: lbm_ordering, keys_dev: int, stream: int) 
     _check(load().lbm_ordering_keys(_dims(dims), ordering, keys_dev, stream))
 
 
-def lbm_build_sparse(flags_dev: int, dims, ordering: lbm_ordering, stream: int) -> int:
+def lbm_build_sparse(flags: int, dims, ordering: lbm_ordering, stream: int) -> int:
     out = ctypes.c_void_p()
-    _check(load().lbm_build_sparse(flags_dev, _dims(dims), ordering, stream, ctypes.byref(out)))
+    _check(load().lbm_build_sparse(flags, _dims(dims), ordering, stream, ctypes.byref(out)))
     return out.value
 
 

@@ -229,12 +229,12 @@ extern "C" int lbm_ordering_keys(const int32_t dims[3], lbm_ordering ord, uint64
   return LBM_OK;
 }
 
-extern "C" int lbm_build_sparse(const uint8_t* flags_dev, const int32_t dims[3], lbm_ordering ord,
+extern "C" int lbm_build_sparse(const uint8_t* flags, const int32_t dims[3], lbm_ordering ord,
                                 void* stream_v, lbm_sparse** out) {
   clear_error();
   if (!out) return fail(LBM_EINVAL, "out is NULL");
   *out = nullptr;
-  if (!flags_dev) return fail(LBM_EINVAL, "flags_dev is NULL");
+  if (!flags) return fail(LBM_EINVAL, "flags is NULL");
   KeySpace ks;
   int rc = make_key_space(dims, ord, true, &ks);
   if (rc) return rc;
@@ -242,11 +242,17 @@ extern "C" int lbm_build_sparse(const uint8_t* flags_dev, const int32_t dims[3],
   const int64_t box = ks.nx * ks.ny * ks.nz;
   const int64_t ntiles = (int64_t)((ks.size + kTileKeys - 1) / kTileKeys);
   if (ntiles >= (int64_t)1 << 31) return fail(LBM_EOVERFLOW, "key space too large");
+  // host flags (pinned or pageable) are copied to the device first
+  cudaPointerAttributes attr{};
+  const cudaError_t pe = cudaPointerGetAttributes(&attr, flags);
+  if (pe != cudaSuccess) return cuda_fail(pe, "cudaPointerGetAttributes(flags)");
+  const bool on_host = attr.type == cudaMemoryTypeHost || attr.type == cudaMemoryTypeUnregistered;
 
   // scratch: tile counts, tile offsets, total, error flag
   uint32_t* counts = nullptr;
   int64_t* offsets = nullptr;
   int64_t* scal = nullptr;  // [0] total, [1] bad-flag word
+  uint8_t* flags_copy = nullptr;
   lbm_sparse* sp = new lbm_sparse{};
   sp->magic = kMagicSparse;
   for (int k = 0; k < 3; ++k) sp->dims[k] = dims[k];
@@ -257,6 +263,7 @@ extern "C" int lbm_build_sparse(const uint8_t* flags_dev, const int32_t dims[3],
     release(counts);
     release(offsets);
     release(scal);
+    release(flags_copy);
     if (status != LBM_OK) {
       release(sp->cells);
       release(sp->inv);
@@ -275,6 +282,18 @@ extern "C" int lbm_build_sparse(const uint8_t* flags_dev, const int32_t dims[3],
   }
   if (cudaMemsetAsync(scal, 0, sizeof(int64_t) * 2, stream) != cudaSuccess)
     return cleanup(cuda_fail(cudaGetLastError(), "cudaMemsetAsync"));
+  const uint8_t* flags_dev = flags;
+  if (on_host) {
+    if (dev_alloc(&flags_copy, (size_t)box, stream, true) != cudaSuccess) {
+      cudaGetLastError();
+      return cleanup(fail(LBM_ENOMEM, "device copy of the host flags (%lld bytes) failed",
+                          (long long)box));
+    }
+    const cudaError_t ce =
+        cudaMemcpyAsync(flags_copy, flags, (size_t)box, cudaMemcpyHostToDevice, stream);
+    if (ce != cudaSuccess) return cleanup(cuda_fail(ce, "cudaMemcpyAsync(flags)"));
+    flags_dev = flags_copy;
+  }
   tile_count_kernel<<<(unsigned)ntiles, kTileThreads, 0, stream>>>(ks, flags_dev, counts,
                                                                   (int*)(scal + 1));
   tile_scan_kernel<<<1, 1024, 0, stream>>>(counts, ntiles, offsets, scal);

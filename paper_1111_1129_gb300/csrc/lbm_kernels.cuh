@@ -467,8 +467,12 @@ __device__ __forceinline__ uint32_t c_to_bits(float v, float scale) {
 // 26,288; one 4-byte store of the pair on the aligned rows 38,823; one
 // 4-byte load for both pulls where they share a word 32,568; storing all 19
 // rows of one cell before the other's 39,063; three or four cells per
-// thread (80 / 128 registers) 33,154 / 28,450 MFLUP/s.  The per-cell
-// arithmetic is that of sweep_kernel, so results are bit-identical to it.
+// thread (80 / 128 registers) 33,154 / 28,450; cells i and i + 32 of a
+// warp's 64 (each access contiguous) 40,189; links loaded before the wait
+// for the previous step 37,263; write-back instead of streaming stores
+// 42,277 against 42,447 MFLUP/s; 2-byte rest-row loads 42,249; 128-thread
+// blocks 41,209.  The per-cell arithmetic is that of sweep_kernel, so
+// results are bit-identical to it.
 #ifndef LBM_PAIR_SWEEP
 #define LBM_PAIR_SWEEP 1
 #endif

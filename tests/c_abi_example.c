@@ -37,12 +37,6 @@ int main(int argc, char** argv) {
       for (int32_t x = 0; x < dims[0]; ++x)
         flags[x + (size_t)dims[0] * (y + (size_t)dims[1] * z)] =
             (x == 0 || y == 0 || x == dims[0] - 1 || y == dims[1] - 1) ? 1 : 0;
-  void* flags_dev = NULL;
-  if (cudaMalloc(&flags_dev, box) != cudaSuccess ||
-      cudaMemcpy(flags_dev, flags, box, cudaMemcpyHostToDevice) != cudaSuccess) {
-    fprintf(stderr, "device copy of the flags failed\n");
-    return 2;
-  }
 
   lbm_ordering ord;
   ord.kind = LBM_ORDER_LEX;
@@ -50,7 +44,8 @@ int main(int argc, char** argv) {
   ord.periodic = 4u; /* z */
   lbm_sparse* sp = NULL;
   lbm_state* st = NULL;
-  check(lbm_build_sparse((const uint8_t*)flags_dev, dims, ord, NULL, &sp), "lbm_build_sparse");
+  /* host flags: the library copies them to the device itself */
+  check(lbm_build_sparse(flags, dims, ord, NULL, &sp), "lbm_build_sparse");
   int64_t n = 0;
   check(lbm_sparse_info(sp, &n, NULL, NULL, NULL), "lbm_sparse_info");
   check(lbm_state_create(sp, LBM_F64X, 0, &st), "lbm_state_create");
@@ -72,7 +67,6 @@ int main(int argc, char** argv) {
 
   lbm_free(st);
   lbm_free(sp);
-  cudaFree(flags_dev);
   free(flags);
   return 0;
 }

@@ -38,17 +38,24 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
-sys.path.insert(0, ROOT)
-
-import oracle  # noqa: E402
-from paper_1111_1129_gb300 import inputs  # noqa: E402
-
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "medium_bed_u_fp64_oracle.npz")
 WP = 1.0 / 0.8
 FORCE = (1e-6, 0.0, 0.0)
 
 
+def load(path: str = OUT) -> dict:
+    """The stored reference as a dict; u as FP64 [3, N] (from its FP32)."""
+    with np.load(path) as z:
+        ref = {k: z[k] for k in z.files}
+    ref["u"] = ref["u"].astype(np.float64)
+    return ref
+
+
 def main() -> int:
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_1111_1129_gb300 import inputs
+
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--chunk", type=int, default=500)

@@ -103,3 +103,27 @@ def test_ordering_tuner_on_a_sample():
     assert best == table[0][:2] and best in [(n, tuple(b)) for n, b in DEFAULT_CANDIDATES]
     assert all(r[2] > 0 for r in table)
     assert [r[2] for r in table] == sorted((r[2] for r in table), reverse=True)
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_build_from_host_flags(pinned):
+    """lbm_build_sparse takes host flags (pageable or pinned) as well as
+    device flags; the result is the same representation bit for bit."""
+    from paper_1111_1129_gb300.lbm import ORDERINGS, _borrow
+    bed = inputs.packed_bed((40, 36, 30), 2, 28.0, 4.0, 0.45, 6)
+    flags = torch.from_numpy(bed.flags)
+    if pinned:
+        flags = flags.pin_memory()
+    stream = int(torch.cuda.current_stream().cuda_stream)
+    h = capi.lbm_build_sparse(flags.data_ptr(), bed.dims,
+                              capi.make_ordering(ORDERINGS["morton1"], (1, 1, 1), bed.periodic),
+                              stream)
+    n, cells_p, adj_p, inv_p = capi.lbm_sparse_info(h)
+    cells, inv, adj = oracle.build_sparse(bed.flags, oracle.ORDER_MORTON1, (1, 1, 1),
+                                          bed.periodic)
+    assert n == len(cells)
+    np.testing.assert_array_equal(_borrow(cells_p, (n,), "<i4", torch.int32).cpu().numpy(), cells)
+    np.testing.assert_array_equal(_borrow(adj_p, (18, n), "<i4", torch.int32).cpu().numpy(), adj)
+    np.testing.assert_array_equal(
+        _borrow(inv_p, bed.flags.shape, "<i4", torch.int32).cpu().numpy(), inv)
+    capi.lbm_free(h)
