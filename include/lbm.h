@@ -383,8 +383,11 @@ void lbm_free(void* handle);
  * Handles take their device memory from a caller-supplied allocator when
  * one is set, else from cudaMalloc (cudaMallocAsync on the handle's stream
  * for the sparse representation and its scratch).
- *   alloc(bytes, stream, ctx) returns a device pointer, or NULL: the calling
- *     function then fails with LBM_ENOMEM.
+ *   alloc(bytes, stream, ctx) returns a device pointer aligned to at least
+ *     16 bytes (cudaMalloc and PyTorch's allocator give 256), or NULL: the
+ *     calling function then fails with LBM_ENOMEM.  A pointer aligned to
+ *     less is given back through release and the call fails the same way
+ *     (the kernels use vector accesses).
  *   release(ptr, stream, ctx) gives a block back.  It may be called while
  *     work queued on `stream` still uses the block, so the allocator must not
  *     hand the block to work on another stream before that work completes

@@ -1,4 +1,5 @@
 // Error reporting, device memory, handle release and version of the C ABI.
+#include <cstdint>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -23,6 +24,10 @@ cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t stream, bool ordered)
   if (g_alloc) {
     void* q = g_alloc(bytes, (void*)stream, g_alloc_ctx);
     if (!q) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<uintptr_t>(q) % 16 != 0) {   // the kernels use vector accesses
+      if (g_release) g_release(q, (void*)stream, g_alloc_ctx);
+      return cudaErrorMemoryAllocation;
+    }
     *p = q;
   } else {
     const cudaError_t e = ordered ? cudaMallocAsync(p, bytes, stream) : cudaMalloc(p, bytes);

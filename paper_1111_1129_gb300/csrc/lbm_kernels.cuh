@@ -456,23 +456,26 @@ __device__ __forceinline__ uint32_t c_to_bits(float v, float scale) {
 
 // ---- two adjacent cells per thread (16-bit forms) ----------------------------
 // A thread updates cells i and i + 1 (i even), so a warp covers 64
-// consecutive cells.  Every access stays a scalar access of one cell, and
-// the two accesses of a row are issued back to back -- both cells' links,
-// both pulls, and, after both collisions, both stores -- so each pair lands
-// on the same sectors at once and L1 and L2 merge them.  With twice the
-// cells in flight per resident warp (64 registers, 4 blocks per SM), the
-// FP16 sweep on the 1024x256x256 bed ran at 42,512 against 40,624 MFLUP/s
-// for one cell per thread (two alternating runs).  In the same runs the
-// variants that differ were slower: 8-byte link loads on the aligned rows
-// 26,288; one 4-byte store of the pair on the aligned rows 38,823; one
-// 4-byte load for both pulls where they share a word 32,568; storing all 19
-// rows of one cell before the other's 39,063; three or four cells per
-// thread (80 / 128 registers) 33,154 / 28,450; cells i and i + 32 of a
-// warp's 64 (each access contiguous) 40,189; links loaded before the wait
-// for the previous step 37,263; write-back instead of streaming stores
-// 42,277 against 42,447 MFLUP/s; 2-byte rest-row loads 42,249; 128-thread
-// blocks 41,209.  The per-cell arithmetic is that of sweep_kernel, so
-// results are bit-identical to it.
+// consecutive cells and has twice the cells in flight at the same 64
+// registers (4 blocks per SM).  The two accesses of a row are issued back to
+// back -- both cells' links, both pulls, and, after both collisions, both
+// stores -- so each pair lands on the same sectors at once and L1 and L2
+// merge them.  Loads stay scalar; a row whose element q N + i is even (every
+// row when N is even, the even rows otherwise) takes the pair's two stores
+// as one 4-byte store, which cuts the store instructions the LSU queue
+// holds.  FP16 on the 1024x256x256 bed, MFLUP/s, alternating runs: one cell
+// per thread 40,579-40,653; pair, all scalar 42,434-42,453; pair with the
+// 4-byte stores (this kernel) 43,307-43,376.  Measured slower in the same
+// runs: 4-byte stores on the other rows too, built with a lane shuffle,
+// 41,923; one 4-byte load for both pulls where they share a word 29,135;
+// 8-byte link loads on the aligned rows 29,844-30,936 (with and without the
+// L2 hint, non-coherent or coherent); link rows through bulk copies into
+// shared memory, completed on an mbarrier 36,780; three or four cells per
+// thread 33,154 / 28,450; cells i and i + 32 of a warp's 64 40,189; links
+// loaded before the wait for the previous step 37,263; write-back stores
+// 42,277 (against 42,447); 2-byte rest-row loads 42,249; 128-thread blocks
+// 41,209.  The per-cell arithmetic is that of sweep_kernel, so results are
+// bit-identical to it.
 #ifndef LBM_PAIR_SWEEP
 #define LBM_PAIR_SWEEP 1
 #endif
@@ -490,23 +493,14 @@ __device__ __forceinline__ uint32_t ld_nc_u32(const uint32_t* p) {
   return v;
 }
 
+// Pulls, both collisions and the stores of the pair (i, i + 1), given their
+// links a (cell i) and b (cell i + 1).
 template <int PREC, bool DAMPED>
-__global__ void __launch_bounds__(kPairThreads, 4 * 256 / kPairThreads)
-    sweep_pair_kernel(const typename Form<PREC>::S* __restrict__ src,
-                      typename Form<PREC>::S* __restrict__ dst, const int32_t* __restrict__ adj,
-                      int32_t n, Coef<float> k, const float* __restrict__ alpha) {
-  static_assert(PREC == LBM_F16S || PREC == LBM_BF16S, "16-bit forms only");
-  const int32_t z = prior_step_done();
-  const int32_t i = 2 * (int32_t)(blockIdx.x * kPairThreads + threadIdx.x) + z;
-  if (i >= n) return;
-  const bool two = i + 1 < n;   // false only for the last cell of an odd-length list
-  int32_t a[18], b[18];
-#pragma unroll
-  for (int q = 0; q < 18; ++q) {
-    const int32_t* p = adj + q * n + i;
-    a[q] = ld_nc(p);
-    b[q] = two ? ld_nc(p + 1) : 0;
-  }
+__device__ __forceinline__ void pair_body(const typename Form<PREC>::S* __restrict__ src,
+                                          typename Form<PREC>::S* __restrict__ dst, int32_t n,
+                                          const Coef<float>& k, const float* __restrict__ alpha,
+                                          int32_t i, bool two, bool odd_n, const int32_t a[18],
+                                          const int32_t b[18]) {
   const unsigned short* src16 = reinterpret_cast<const unsigned short*>(src);
   // pulled values, packed: low half cell i, high half cell i + 1
   uint32_t g[19];
@@ -540,9 +534,35 @@ __global__ void __launch_bounds__(kPairThreads, 4 * 256 / kPairThreads)
   unsigned short* dst16 = reinterpret_cast<unsigned short*>(dst);
 #pragma unroll
   for (int q = 0; q < 19; ++q) {
-    st_cs(dst16 + q * n + i, (unsigned short)(out[q] & 0xffffu));
-    if (two) st_cs(dst16 + q * n + i + 1, (unsigned short)(out[q] >> 16));
+    const int32_t e = q * n + i;
+    if (two && !(odd_n && (q & 1))) {   // element e is even: one 4-byte store of the pair
+      asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(dst16 + e), "r"(out[q]) : "memory");
+    } else {
+      st_cs(dst16 + e, (unsigned short)(out[q] & 0xffffu));
+      if (two) st_cs(dst16 + e + 1, (unsigned short)(out[q] >> 16));
+    }
   }
+}
+
+template <int PREC, bool DAMPED>
+__global__ void __launch_bounds__(kPairThreads, 4 * 256 / kPairThreads)
+    sweep_pair_kernel(const typename Form<PREC>::S* __restrict__ src,
+                      typename Form<PREC>::S* __restrict__ dst, const int32_t* __restrict__ adj,
+                      int32_t n, Coef<float> k, const float* __restrict__ alpha) {
+  static_assert(PREC == LBM_F16S || PREC == LBM_BF16S, "16-bit forms only");
+  const int32_t z = prior_step_done();
+  const int32_t i = 2 * (int32_t)(blockIdx.x * kPairThreads + threadIdx.x) + z;
+  if (i >= n) return;
+  const bool two = i + 1 < n;   // false only for the last cell of an odd-length list
+  const bool odd_n = (n & 1) != 0;
+  int32_t a[18], b[18];
+#pragma unroll
+  for (int q = 0; q < 18; ++q) {
+    const int32_t* p = adj + q * n + i;
+    a[q] = ld_nc(p);
+    b[q] = two ? ld_nc(p + 1) : 0;
+  }
+  pair_body<PREC, DAMPED>(src, dst, n, k, alpha, i, two, odd_n, a, b);
 }
 
 // Per-cell moments of the collision that a step from `src` performs.

@@ -36,19 +36,34 @@ namespace lbm {
 
 namespace {
 
+// Stored value of every slot of row q at rest, in the storage form: w_q, or
+// the deviation 0 for the shifted forms.
+template <int PREC>
+struct RestRow {
+  typename Form<PREC>::S v[19];
+};
+
+// One row q = blockIdx.y per grid row, so no slot index is divided by N.
+// From rest the stored value comes from `rest`; from f the value is
+// converted as the form stores it (the deviation f - w in FP64, then
+// rounded).
 template <int PREC>
 __global__ void set_pdfs_kernel(typename Form<PREC>::S* __restrict__ dst,
                                 const double* __restrict__ f, int32_t n, double scale,
-                                int from_rest) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 19 * (int64_t)n) return;
-  const int q = (int)(t / n);
-  const double w = weight(q);
-  const double v = from_rest ? w : f[t];
+                                RestRow<PREC> rest) {
+  const int q = (int)blockIdx.y;
+  const int32_t i = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= n) return;
+  const int64_t t = (int64_t)q * n + i;
+  if (!f) {
+    dst[t] = rest.v[q];
+    return;
+  }
   using C = typename Form<PREC>::C;
+  const double w = weight(q);
   C c;
-  if constexpr (Form<PREC>::kShifted) c = (C)(v - w);
-  else c = (C)v;
+  if constexpr (Form<PREC>::kShifted) c = (C)(f[t] - w);
+  else c = (C)f[t];
   dst[t] = encode<PREC>(c, (C)scale);
 }
 
@@ -182,9 +197,21 @@ int launch_set(lbm_state* st, const double* f, int from_rest) {
   const int64_t total = 19 * st->sp->n;
   if (total == 0) return LBM_OK;
   const bool grouped = batch_grouped(st);
-  set_pdfs_kernel<PREC><<<(unsigned)((total + 255) / 256), 256, 0, st->sp->stream>>>(
-      (typename Form<PREC>::S*)st->buf[grouped ? st->cur ^ 1 : st->cur], f, (int32_t)st->sp->n,
-      std::ldexp(1.0, st->scale_exp), from_rest);
+  using S = typename Form<PREC>::S;
+  using C = typename Form<PREC>::C;
+  RestRow<PREC> rest;
+  for (int q = 0; q < 19; ++q) {
+    const double w = weight(q);
+    if constexpr (Form<PREC>::kShifted) {
+      rest.v[q] = S{};   // a zero deviation: all-zero bits in every shifted form
+    } else {
+      rest.v[q] = (S)(C)w;
+    }
+  }
+  const int32_t n = (int32_t)st->sp->n;
+  set_pdfs_kernel<PREC><<<dim3((unsigned)((n + 255) / 256), 19), 256, 0, st->sp->stream>>>(
+      (S*)st->buf[grouped ? st->cur ^ 1 : st->cur], from_rest ? nullptr : f, n,
+      std::ldexp(1.0, st->scale_exp), rest);
   LBM_CUDA_TRY(cudaGetLastError());
   if (grouped) return batch_relayout_pdfs(st, st->cur ^ 1, st->cur, false);
   return LBM_OK;
@@ -372,7 +399,10 @@ extern "C" int lbm_state_create(const lbm_sparse* sp, int32_t precision, int32_t
     return fail(LBM_ENOMEM, "state allocation of 2 x %zu bytes failed", bytes);
   }
   int rc = dispatch_set(st, nullptr, 1);
-  if (rc == LBM_OK) {
+  // The first step writes every slot of the second grid before anything
+  // reads it.  A concatenated batch (ord.kind -1) also has padding cells
+  // that no step writes: zero its second grid so that they read back as 0.
+  if (rc == LBM_OK && sp->ord.kind == -1) {
     const cudaError_t e = cudaMemsetAsync(st->buf[1], 0, bytes, sp->stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync");
   }
