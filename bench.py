@@ -53,7 +53,6 @@ BYTES_PER_LUP = {"f64": 19 * 8 * 2 + 18 * 4, "f64x": 19 * 8 * 2 + 18 * 4,
 # kernel changes.
 MEASURED_DRAM_BYTES_PER_LUP = {
     ("large", "f64x", "lex"): 379.1, ("large", "f32s", "lex"): 223.3,
-    ("large", "f16s", "lex"): 147.3,
 }
 STORAGE = {"f64": "f64", "f64x": "f64", "f32": "f32", "f32s": "f32 (f - w)",
            "f16s": "f16 ((f - w) 2^k)", "bf16s": "bf16 ((f - w) 2^k)"}
@@ -514,7 +513,8 @@ def run_adjoint_study(args):
     alpha = torch.from_numpy(alpha_dense.reshape(-1)[lat.cells().cpu().numpy()].copy()).cuda()
     K, stride, F = args.adjoint_steps, 45, (0.0, 0.0, 1e-6)
     out = {}
-    for prec in ("f32s", "f64"):
+    ref_f64 = None
+    for prec in args.adjoint_forms.split(","):
         st = LBMState(lat, prec)
         st.set_damping(alpha)
 
@@ -536,11 +536,20 @@ def run_adjoint_study(args):
         J, t_af = timed(lambda: adj.forward(WP, wm, F, 2))
         (dF, da, _), t_ab = timed(lambda: adj.backward())
         state_bytes = lat.n * 19 * (4 if prec == "f32s" else 8)
+        # the FP64 forms' gradients against each other (f64: IEEE FP64
+        # arithmetic; f64x: fixed-point steps, double-single reverse steps)
+        if prec == "f64":
+            ref_f64 = (dF, da.clone())
+        if prec == "f64x" and ref_f64 is not None:
+            rel_dF = max(abs(a - b) for a, b in zip(dF, ref_f64[0])) / max(abs(v) for v in ref_f64[0])
+            rel_da = float(torch.linalg.norm(da - ref_f64[1]) / torch.linalg.norm(ref_f64[1]))
         out[prec] = {"forward_s": t_fwd, "adjoint_forward_s": t_af, "adjoint_backward_s": t_ab,
                      "adjoint_total_over_forward": (t_af + t_ab) / t_fwd,
                      "adjoint_device_bytes": held,
                      "adjoint_bytes_over_one_state": held / state_bytes,
                      "J": J, "dJdFz": dF[2]}
+        if prec == "f64x" and ref_f64 is not None:
+            out[prec]["vs_f64"] = {"dJdF_rel": rel_dF, "dJdalpha_norm_rel": rel_da}
         adj.close()
         st.close()
     line = {"study": "adjoint", "workload": "packed bed 128^3, tube D=126 along z, spheres r=6, "
@@ -777,6 +786,7 @@ def main():
     ap.add_argument("--adjoint-study", action="store_true",
                     help="time the checkpointed adjoint against the forward run")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--adjoint-forms", default="f32s,f64,f64x")
     args = ap.parse_args()
     if args.adjoint_study:
         return run_adjoint_study(args)
