@@ -37,6 +37,7 @@
 struct lbm_adjoint {
   uint32_t magic;
   const lbm_state* st;
+  cudaStream_t stream;   // the state's stream, kept so that freeing needs no state
   int32_t K, stride, n_ckpt;
   void* ckpt;       // n_ckpt states of 19 N storage elements
   void* seg;        // max(stride, 2) states
@@ -243,6 +244,300 @@ __global__ void __launch_bounds__(kSweepThreads)
   block_accumulate4(red, part + z + 4 * (int64_t)blockIdx.x, false);
 }
 
+// ---- FP64-storage adjoint in double-single arithmetic --------------------------
+// For LBM_F64X the reverse step keeps FP64-level accuracy without FP64
+// instructions on its common path.  lambda is stored as a pair of FP32
+// values (hi, lo) whose unevaluated sum carries ~48 significant bits, and
+// is computed with error-free transformations: Knuth's TwoSum, Dekker's
+// Fast2Sum (|a| >= |b|), and the product of two FP32 values with its exact
+// error from one FMA (Ogita, Rump and Oishi, 2005).  The forward velocity
+// comes exact from the FP64 bit patterns in 64-bit fixed point, as in the
+// fixed-point sweep (units 2^-58), damping included (u - e u); a cell whose
+// PDFs leave their binary ranges computes it in FP64 instead.
+struct ds {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ds ds_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ds ds_fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ ds ds_add(ds x, ds y) {
+  const ds s = ds_two_sum(x.hi, y.hi);
+  return ds_fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ ds ds_neg(ds x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ ds ds_sub(ds x, ds y) { return ds_add(x, ds_neg(y)); }
+__device__ __forceinline__ ds ds_mul(ds x, ds y) {
+  const float p = x.hi * y.hi;
+  const float e = fmaf(x.hi, y.hi, -p);
+  return ds_fast_two_sum(p, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e)));
+}
+// x times a power of two c (exact, barring overflow and underflow)
+__device__ __forceinline__ ds ds_scale_pow2(ds x, float c) { return {x.hi * c, x.lo * c}; }
+__device__ __forceinline__ double ds_to_double(ds x) { return (double)x.hi + (double)x.lo; }
+// Host and device: the pair nearest to v (|lo| <= ulp(hi)/2).
+__host__ __device__ __forceinline__ ds ds_from_double(double v) {
+  const float hi = (float)v;
+  return {hi, (float)(v - (double)hi)};
+}
+// An int64 value in units 2^-sc (sc = 58 or 63, |v| < 2^62), to ~48 bits.
+__device__ __forceinline__ ds ds_from_fixed(int64_t v, int sc) {
+  const float hi = (float)v;   // round to nearest
+  const int64_t rest = v - (int64_t)hi;
+  const float lo = (float)rest;
+  const float scale = sc == 58 ? 0x1p-58f : 0x1p-63f;   // exact: powers of two
+  return {hi * scale, lo * scale};
+}
+
+// Coefficients of the reverse step as pairs.
+struct AdjCoefDS {
+  ds wp, one_m_wp, k1, k2, three_wm, src, three_src, nine_wp, three_wp, inv_n;
+  ds w0, w1, w2, hF[3];
+  int64_t fhF[3];   // F/2 in units 2^-58, for the fixed-point velocity
+};
+
+AdjCoefDS make_adj_coef_ds(double wp, double wm, const double F[3], int64_t n) {
+  AdjCoefDS a;
+  a.wp = ds_from_double(wp);
+  a.one_m_wp = ds_from_double(1.0 - wp);
+  a.k1 = ds_from_double(1.0 - 0.5 * (wp + wm));
+  a.k2 = ds_from_double(0.5 * (wm - wp));
+  a.three_wm = ds_from_double(3.0 * wm);
+  a.src = ds_from_double(1.0 - 0.5 * wm);
+  a.three_src = ds_from_double(3.0 * (1.0 - 0.5 * wm));
+  a.nine_wp = ds_from_double(9.0 * wp);
+  a.three_wp = ds_from_double(3.0 * wp);
+  a.inv_n = ds_from_double(n > 0 ? 1.0 / (double)n : 0.0);
+  a.w0 = ds_from_double(1.0 / 3.0);
+  a.w1 = ds_from_double(1.0 / 18.0);
+  a.w2 = ds_from_double(1.0 / 36.0);
+  for (int d = 0; d < 3; ++d) {
+    a.hF[d] = ds_from_double(0.5 * F[d]);
+    a.fhF[d] = (int64_t)std::llround(0.5 * F[d] * 0x1p58);
+  }
+  return a;
+}
+
+constexpr int64_t kAdjW0Bits = 0x3FD5555555555555LL;  // bits of 1/3, 1/18, 1/36
+constexpr int64_t kAdjW1Bits = 0x3FAC71C71C71C71CLL;
+constexpr int64_t kAdjW2Bits = 0x3F9C71C71C71C71CLL;
+
+// Velocity and damping factor s = 1/(1 + alpha/2) of the collision of the
+// pulled FP64 values g, as pairs: from the bit patterns in fixed point where
+// every value lies in its weight's binary range (and alpha in [0, 1/2)),
+// else in FP64.
+template <bool DAMPED>
+__device__ __forceinline__ void ds_velocity(const double g[19], const AdjCoefDS& a,
+                                            const Coef<double>& kd,
+                                            const double* __restrict__ alpha,
+                                            const int64_t* __restrict__ alpha_fx, int32_t n,
+                                            int32_t i, ds u[3], ds& s) {
+  bool fast = true;
+  int64_t X[19];
+#pragma unroll
+  for (int q = 0; q < 19; ++q) {
+    const int64_t b = __double_as_longlong(g[q]);
+    const int64_t wb = q == 0 ? kAdjW0Bits : (q <= 6 ? kAdjW1Bits : kAdjW2Bits);
+    const int sh = q == 0 ? 4 : (q <= 6 ? 1 : 0);
+    fast &= (b >> 52) == (wb >> 52);
+    X[q] = (b - wb) << sh;   // exact deviation in units 2^-58 when in range
+  }
+  int64_t E = 0;
+  if constexpr (DAMPED) {
+    const int64_t A = __ldg(alpha_fx + i);
+    fast &= A >= 0;
+    E = __ldg(alpha_fx + n + i);
+  }
+  if (fast) {
+    int64_t D[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) D[p] = X[2 * p + 1] - X[2 * p + 2];
+    int64_t j[3] = {(((D[0] + D[3]) + (D[4] + D[5])) + D[6]) + a.fhF[0],
+                    (((D[1] + D[3]) - (D[4] - D[7])) + D[8]) + a.fhF[1],
+                    (((D[2] + D[5]) - (D[6] - D[7])) - D[8]) + a.fhF[2]};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if constexpr (DAMPED) j[d] -= __mul64hi(2 * j[d], E);   // u = j - e j
+      u[d] = ds_from_fixed(j[d], 58);
+    }
+    s = DAMPED ? ds_sub(ds{1.f, 0.f}, ds_from_fixed(E, 63)) : ds{1.f, 0.f};
+  } else {
+    double ud[3], sd;
+    velocity<double, DAMPED>(g, kd, DAMPED ? alpha[i] : 0.0, ud, sd);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) u[d] = ds_from_double(ud[d]);
+    s = ds_from_double(sd);
+  }
+}
+
+// Block sums of four pairs, added to acc[4] in FP64 (as block_accumulate4).
+__device__ __forceinline__ void block_accumulate4_ds(ds v[4], double* acc, bool assign) {
+  __shared__ double sm[kSweepThreads / 32][4];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const ds w = {__shfl_down_sync(0xffffffffu, v[j].hi, o),
+                    __shfl_down_sync(0xffffffffu, v[j].lo, o)};
+      v[j] = ds_add(v[j], w);
+    }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sm[warp][j] = ds_to_double(v[j]);
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kSweepThreads / 32; ++w) t += sm[w][threadIdx.x];
+    acc[threadIdx.x] = assign ? t : acc[threadIdx.x] + t;
+  }
+}
+
+// Seed of the FP64-storage adjoint: as adjoint_seed_kernel, lambda written
+// as pairs (float2 [19][N]).
+template <bool DAMPED>
+__global__ void __launch_bounds__(kSweepThreads)
+    adjoint_seed_ds_kernel(const double* __restrict__ f_prev, const int32_t* __restrict__ adj,
+                           int32_t n, Coef<double> k, AdjCoef<double> a,
+                           const double* __restrict__ alpha, int axis, float2* __restrict__ lam_out,
+                           double* __restrict__ part, double* __restrict__ dalpha) {
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < n) {
+    double g[19];
+    gather<LBM_F64>(f_prev, adj, n, i, 1.0, g);
+    double u[3], s;
+    const double al = DAMPED ? alpha[i] : 0.0;
+    velocity<double, DAMPED>(g, k, al, u, s);
+    const double seed = s * a.inv_n;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+      const ds v = ds_from_double((double)axis_component(q, axis) * seed);
+      lam_out[q * n + i] = make_float2(v.hi, v.lo);
+    }
+    red[axis] = 0.5 * seed;
+    red[3] = u[axis];
+    dalpha[i] = -0.5 * seed * u[axis];
+  }
+  block_accumulate4(red, part + 4 * (int64_t)blockIdx.x, true);
+}
+
+// One reverse step of the FP64-storage adjoint (adjoint_step_kernel's
+// formulas) in double-single arithmetic.
+template <bool DAMPED>
+__global__ void __launch_bounds__(kSweepThreads)
+    adjoint_step_ds_kernel(const double* __restrict__ f_prev, const int32_t* __restrict__ adj,
+                           int32_t n, Coef<double> kd, AdjCoefDS a,
+                           const double* __restrict__ alpha, const int64_t* __restrict__ alpha_fx,
+                           const float2* __restrict__ lam_in, float2* __restrict__ lam_out,
+                           double* __restrict__ part, double* __restrict__ dalpha) {
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  ds red[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  if (i < n) {
+    int32_t idx[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) idx[q] = __ldg(adj + q * n + i);
+    double g[19];
+    float2 l2[19];
+    g[0] = ld_nc(f_prev + i);
+#pragma unroll
+    for (int q = 1; q < 19; ++q) g[q] = ld_nc(f_prev + idx[q - 1]);
+    l2[0] = __ldg(lam_in + i);
+#pragma unroll
+    for (int q = 1; q < 19; ++q) l2[q] = __ldg(lam_in + reverse_slot(q, idx[opp(q) - 1], n, i));
+    ds u[3], s;
+    ds_velocity<DAMPED>(g, a, kd, alpha, alpha_fx, n, i, u, s);
+    ds lf[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) lf[q] = {l2[q].x, l2[q].y};
+    ds S[9], D[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      S[p] = ds_add(lf[2 * p + 1], lf[2 * p + 2]);
+      D[p] = ds_sub(lf[2 * p + 1], lf[2 * p + 2]);
+    }
+    const ds M0 = ds_add(ds_add(ds_mul(a.w0, lf[0]), ds_mul(a.w1, ds_add(ds_add(S[0], S[1]), S[2]))),
+                         ds_mul(a.w2, ds_add(ds_add(ds_add(S[3], S[4]), ds_add(S[5], S[6])),
+                                             ds_add(S[7], S[8]))));
+    const ds M1x = ds_add(ds_mul(a.w1, D[0]), ds_mul(a.w2, ds_add(ds_add(D[3], D[4]), ds_add(D[5], D[6]))));
+    const ds M1y = ds_add(ds_mul(a.w1, D[1]), ds_mul(a.w2, ds_add(ds_sub(D[3], D[4]), ds_add(D[7], D[8]))));
+    const ds M1z = ds_add(ds_mul(a.w1, D[2]), ds_mul(a.w2, ds_add(ds_sub(D[5], D[6]), ds_sub(D[7], D[8]))));
+    const ds Mxx = ds_add(ds_mul(a.w1, S[0]), ds_mul(a.w2, ds_add(ds_add(S[3], S[4]), ds_add(S[5], S[6]))));
+    const ds Myy = ds_add(ds_mul(a.w1, S[1]), ds_mul(a.w2, ds_add(ds_add(S[3], S[4]), ds_add(S[7], S[8]))));
+    const ds Mzz = ds_add(ds_mul(a.w1, S[2]), ds_mul(a.w2, ds_add(ds_add(S[5], S[6]), ds_add(S[7], S[8]))));
+    const ds Mxy = ds_mul(a.w2, ds_sub(S[3], S[4]));
+    const ds Mxz = ds_mul(a.w2, ds_sub(S[5], S[6]));
+    const ds Myz = ds_mul(a.w2, ds_sub(S[7], S[8]));
+    const ds three_wp_m0 = ds_mul(a.three_wp, M0);
+    // beta = 3 (w- - alpha (1 - w-/2)); alpha from its fixed-point value
+    ds beta = a.three_wm;
+    if constexpr (DAMPED) {
+      const int64_t A = __ldg(alpha_fx + i);
+      const ds al = A >= 0 ? ds_from_fixed(A, 63) : ds_from_double(alpha[i]);
+      beta = ds_sub(beta, ds_mul(a.three_src, al));
+    }
+    const ds Gx = ds_add(ds_sub(ds_mul(a.nine_wp, ds_add(ds_add(ds_mul(Mxx, u[0]), ds_mul(Mxy, u[1])), ds_mul(Mxz, u[2]))),
+                                ds_mul(three_wp_m0, u[0])), ds_mul(beta, M1x));
+    const ds Gy = ds_add(ds_sub(ds_mul(a.nine_wp, ds_add(ds_add(ds_mul(Mxy, u[0]), ds_mul(Myy, u[1])), ds_mul(Myz, u[2]))),
+                                ds_mul(three_wp_m0, u[1])), ds_mul(beta, M1y));
+    const ds Gz = ds_add(ds_sub(ds_mul(a.nine_wp, ds_add(ds_add(ds_mul(Mxz, u[0]), ds_mul(Myz, u[1])), ds_mul(Mzz, u[2]))),
+                                ds_mul(three_wp_m0, u[2])), ds_mul(beta, M1z));
+    const ds base = ds_mul(a.wp, M0);
+    {
+      const ds v = ds_add(ds_mul(a.one_m_wp, lf[0]), base);
+      lam_out[i] = make_float2(v.hi, v.lo);
+    }
+#define LBM_ADJ_DS_PAIR(P, CG)                                                                  \
+  {                                                                                             \
+    const ds sg_ = ds_mul(s, (CG));                                                             \
+    const ds va_ = ds_add(ds_add(ds_add(ds_mul(a.k1, lf[2 * P + 1]), ds_mul(a.k2, lf[2 * P + 2])), base), sg_); \
+    const ds vb_ = ds_sub(ds_add(ds_add(ds_mul(a.k1, lf[2 * P + 2]), ds_mul(a.k2, lf[2 * P + 1])), base), sg_); \
+    lam_out[(2 * P + 1) * n + i] = make_float2(va_.hi, va_.lo);                                \
+    lam_out[(2 * P + 2) * n + i] = make_float2(vb_.hi, vb_.lo);                                \
+  }
+    LBM_ADJ_DS_PAIR(0, Gx)
+    LBM_ADJ_DS_PAIR(1, Gy)
+    LBM_ADJ_DS_PAIR(2, Gz)
+    LBM_ADJ_DS_PAIR(3, ds_add(Gx, Gy))
+    LBM_ADJ_DS_PAIR(4, ds_sub(Gx, Gy))
+    LBM_ADJ_DS_PAIR(5, ds_add(Gx, Gz))
+    LBM_ADJ_DS_PAIR(6, ds_sub(Gx, Gz))
+    LBM_ADJ_DS_PAIR(7, ds_add(Gy, Gz))
+    LBM_ADJ_DS_PAIR(8, ds_sub(Gy, Gz))
+#undef LBM_ADJ_DS_PAIR
+    const ds hs = ds_scale_pow2(s, 0.5f);
+    red[0] = ds_add(ds_mul(hs, Gx), ds_mul(a.three_src, M1x));
+    red[1] = ds_add(ds_mul(hs, Gy), ds_mul(a.three_src, M1y));
+    red[2] = ds_add(ds_mul(hs, Gz), ds_mul(a.three_src, M1z));
+    const ds Gu = ds_add(ds_add(ds_mul(Gx, u[0]), ds_mul(Gy, u[1])), ds_mul(Gz, u[2]));
+    const ds M1u = ds_add(ds_add(ds_mul(M1x, u[0]), ds_mul(M1y, u[1])), ds_mul(M1z, u[2]));
+    dalpha[i] += ds_to_double(ds_neg(ds_add(ds_mul(hs, Gu), ds_mul(a.three_src, M1u))));
+  }
+  block_accumulate4_ds(red, part + 4 * (int64_t)blockIdx.x, false);
+}
+
+// lam_f_0 of the FP64-storage adjoint (lambda as pairs).
+__global__ void __launch_bounds__(kSweepThreads)
+    adjoint_initial_ds_kernel(const int32_t* __restrict__ adj, int32_t n,
+                              const float2* __restrict__ lam_in, double* __restrict__ out) {
+  const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
+  if (i >= n) return;
+  const float2 v0 = lam_in[i];
+  out[i] = (double)v0.x + (double)v0.y;
+#pragma unroll
+  for (int q = 1; q < 19; ++q) {
+    const float2 v = lam_in[reverse_slot(q, adj[(opp(q) - 1) * n + i], n, i)];
+    out[q * n + i] = (double)v.x + (double)v.y;
+  }
+}
+
 // lam_f_0 = S^T lam_g_1 (gradient with respect to the initial PDFs).
 template <class C>
 __global__ void __launch_bounds__(kSweepThreads)
@@ -278,6 +573,7 @@ struct Runner {
   mutable bool chained = false;
   mutable cudaError_t err = cudaSuccess;
 
+  AdjCoefDS ads;   // LBM_F64X: the reverse step in double-single arithmetic
   Runner(lbm_adjoint* ad_) : ad(ad_), st(ad_->st) {
     n = (int32_t)st->sp->n;
     stream = st->sp->stream;
@@ -286,7 +582,9 @@ struct Runner {
     a = make_adj_coef<C>(ad->wp, ad->wm, n);
     alpha = (const C*)st->alpha;
     state_elems = 19 * (size_t)n;
+    if constexpr (PREC == LBM_F64X) ads = make_adj_coef_ds(ad->wp, ad->wm, ad->F, n);
   }
+  float2* lam2(int i) const { return (float2*)ad->lam[i]; }
   S* ckpt(int j) const { return (S*)ad->ckpt + (size_t)j * state_elems; }
   S* seg(int i) const { return (S*)ad->seg + (size_t)i * state_elems; }
   C* lam(int i) const { return (C*)ad->lam[i]; }
@@ -298,14 +596,34 @@ struct Runner {
     chained = true;
   }
   void step(const S* src, S* dst) const {
+    if constexpr (PREC == LBM_F64X) {
+      // FP64 storage: the fixed-point sweep, as lbm_step takes it
+      const int rc = launch_fx_step(st, (const double*)src, (double*)dst, ad->wp, ad->wm, ad->F,
+                                    stream, false);
+      if (rc != LBM_OK && err == cudaSuccess) err = cudaErrorLaunchFailure;
+      chained = true;
+      return;
+    }
     if (alpha) launch(sweep_kernel<PREC, true, kNoReduce>, src, dst, st->sp->adj, n, k, alpha, (double*)nullptr);
     else launch(sweep_kernel<PREC, false, kNoReduce>, src, dst, st->sp->adj, n, k, alpha, (double*)nullptr);
   }
   void seed(const S* f_prev) const {
+    if constexpr (PREC == LBM_F64X) {
+      const double* al = (const double*)alpha;
+      if (alpha) launch(adjoint_seed_ds_kernel<true>, (const double*)f_prev, st->sp->adj, n, k, a, al, ad->axis, lam2(0), ad->part, ad->dalpha);
+      else launch(adjoint_seed_ds_kernel<false>, (const double*)f_prev, st->sp->adj, n, k, a, al, ad->axis, lam2(0), ad->part, ad->dalpha);
+      return;
+    }
     if (alpha) launch(adjoint_seed_kernel<PREC, true>, f_prev, st->sp->adj, n, k, a, alpha, ad->axis, lam(0), ad->part, ad->dalpha);
     else launch(adjoint_seed_kernel<PREC, false>, f_prev, st->sp->adj, n, k, a, alpha, ad->axis, lam(0), ad->part, ad->dalpha);
   }
   void reverse(const S* f_prev, int in) const {
+    if constexpr (PREC == LBM_F64X) {
+      const double* al = (const double*)alpha;
+      if (alpha) launch(adjoint_step_ds_kernel<true>, (const double*)f_prev, st->sp->adj, n, k, ads, al, (const int64_t*)st->alpha_fx, (const float2*)lam2(in), lam2(in ^ 1), ad->part, ad->dalpha);
+      else launch(adjoint_step_ds_kernel<false>, (const double*)f_prev, st->sp->adj, n, k, ads, al, (const int64_t*)st->alpha_fx, (const float2*)lam2(in), lam2(in ^ 1), ad->part, ad->dalpha);
+      return;
+    }
     if (alpha) launch(adjoint_step_kernel<PREC, true>, f_prev, st->sp->adj, n, k, a, alpha, lam(in), lam(in ^ 1), ad->part, ad->dalpha);
     else launch(adjoint_step_kernel<PREC, false>, f_prev, st->sp->adj, n, k, a, alpha, lam(in), lam(in ^ 1), ad->part, ad->dalpha);
   }
@@ -353,8 +671,12 @@ struct Runner {
       reverse(state_at(j, (t - 1) - j * s), in);
       in ^= 1;
     }
-    if (dJdf0)
-      adjoint_initial_kernel<C><<<grid, kSweepThreads, 0, stream>>>(st->sp->adj, n, lam(in), dJdf0);
+    if (dJdf0) {
+      if constexpr (PREC == LBM_F64X)
+        adjoint_initial_ds_kernel<<<grid, kSweepThreads, 0, stream>>>(st->sp->adj, n, lam2(in), dJdf0);
+      else
+        adjoint_initial_kernel<C><<<grid, kSweepThreads, 0, stream>>>(st->sp->adj, n, lam(in), dJdf0);
+    }
     LBM_CUDA_TRY(err);
     LBM_CUDA_TRY(cudaGetLastError());
     return LBM_OK;
@@ -416,7 +738,9 @@ int finish_sums(lbm_adjoint* ad) {
 
 void free_adjoint(lbm_adjoint* ad) {
   if (!ad) return;
-  const cudaStream_t s = ad->st ? ad->st->sp->stream : nullptr;
+  // the state may already be released (a garbage collector may free the two
+  // in either order): only the stream kept here is used
+  const cudaStream_t s = ad->stream;
   cudaStreamSynchronize(s);
   for (void* p : {ad->ckpt, ad->seg, ad->lam[0], ad->lam[1], (void*)ad->part,
                   (void*)ad->dalpha, (void*)ad->red_dev})
@@ -445,6 +769,7 @@ extern "C" int lbm_adjoint_create(const lbm_state* st, int32_t n_steps, int32_t 
   lbm_adjoint* ad = new lbm_adjoint{};
   ad->magic = kMagicAdjoint;
   ad->st = st;
+  ad->stream = st->sp->stream;
   ad->K = n_steps;
   ad->stride = stride;
   ad->n_ckpt = (n_steps - 1) / stride + 1;

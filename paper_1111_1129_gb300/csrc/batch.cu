@@ -578,7 +578,7 @@ void free_batch(lbm_state* st) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->capture) cudaStreamDestroy(b->capture);
-  const cudaStream_t stream = st->sp ? st->sp->stream : nullptr;
+  const cudaStream_t stream = st->stream;
   cudaStreamSynchronize(stream);
   for (void* p : {(void*)b->d_begin, (void*)b->d_count, (void*)b->d_chunk_bed, b->d_force,
                   (void*)b->d_red})

@@ -329,11 +329,14 @@ cudaError_t launch_sweep(void (*kernel)(P...), unsigned grid, cudaStream_t strea
 struct lbm_state {
   uint32_t magic;
   const lbm_sparse* sp;
+  cudaStream_t stream;   // sp's stream, kept so that releasing the state needs no sp
   int32_t precision;
   int32_t scale_exp;
   void* buf[2];        // PDF grids, [19 * n] elements of the storage type
   int cur;             // index of the grid holding the current PDFs
   void* alpha;         // [n] damping in the arithmetic precision, or nullptr
+  int64_t* alpha_fx;   // LBM_F64X with damping: [2][n] alpha 2^63 (-1: the cell takes the
+                       // IEEE path) and e 2^63, e = (alpha/2) / (1 + alpha/2)
   double* partials;    // [nblocks * kWarpsPerBlock * 4] FP64 warp sums of the last step,
                        // then [nblocks * 4] block values formed by lbm_reduce_flux
   int64_t nblocks;
@@ -358,6 +361,13 @@ size_t compute_bytes(int prec);   // bytes of the arithmetic type of a form
 bool is_shifted(int prec);        // stores f - w_q rather than f
 // Fixed-point FP64-storage sweep (sweep_fx.cu), undamped: n_steps launches
 // on `stream`; the last one writes the warp sums when reduce_last is set.
+// One fixed-point step of FP64-storage state st from src to dst (not
+// reducing), queued on `stream`.
+int launch_fx_step(const lbm_state* st, const double* src, double* dst, double wp, double wm,
+                   const double F[3], cudaStream_t stream, bool chained);
+// Fills the fixed-point damping rows (alpha_fx) of an FP64-storage state
+// from FP64 alpha on the device.
+int set_alpha_fx(lbm_state* st, const double* alpha_dev);
 int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3],
                     cudaStream_t stream, bool reduce_last);
 bool valid_state(const lbm_state* st);

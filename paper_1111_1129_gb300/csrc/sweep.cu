@@ -124,9 +124,7 @@ int launch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const dou
   using S = typename Form<PREC>::S;
   using C = typename Form<PREC>::C;
   const int32_t n = (int32_t)st->sp->n;
-  if constexpr (PREC == LBM_F64X) {
-    if (!st->alpha) return launch_steps_fx(st, n_steps, wp, wm, F, stream, reduce_last);
-  }
+  if constexpr (PREC == LBM_F64X) return launch_steps_fx(st, n_steps, wp, wm, F, stream, reduce_last);
   const Coef<C> k = make_coef<C>(wp, wm, F, st->scale_exp);
   const unsigned grid = (unsigned)st->nblocks;
   const C* alpha = (const C*)st->alpha;
@@ -340,9 +338,12 @@ int dispatch_moments(const lbm_state* st, double* rho, double* u) {
 
 void free_state(lbm_state* st) {
   if (!st) return;
-  const cudaStream_t s = st->sp ? st->sp->stream : nullptr;
+  // the sparse handle may already be released (a garbage collector may free
+  // the two in either order): only the stream kept here is used
+  const cudaStream_t s = st->stream;
   cudaStreamSynchronize(s);
-  for (void* p : {st->buf[0], st->buf[1], st->alpha, (void*)st->partials, (void*)st->red_dev})
+  for (void* p : {st->buf[0], st->buf[1], st->alpha, (void*)st->alpha_fx, (void*)st->partials,
+                  (void*)st->red_dev})
     dev_free(p, s, false);
   if (st->red_host) cudaFreeHost(st->red_host);
   if (st->done) cudaEventDestroy(st->done);
@@ -371,6 +372,7 @@ extern "C" int lbm_state_create(const lbm_sparse* sp, int32_t precision, int32_t
   lbm_state* st = new lbm_state{};
   st->magic = kMagicState;
   st->sp = sp;
+  st->stream = sp->stream;
   st->precision = precision;
   st->scale_exp = (precision == LBM_F16S || precision == LBM_BF16S) ? scale_exp : 0;
   const int64_t n = sp->n;
@@ -444,26 +446,38 @@ extern "C" int lbm_set_damping(lbm_state* st, const double* alpha_dev) {
     if (st->alpha) {
       cudaStreamSynchronize(st->sp->stream);
       dev_free(st->alpha, st->sp->stream, false);
+      dev_free(st->alpha_fx, st->sp->stream, false);
     }
     st->alpha = nullptr;
+    st->alpha_fx = nullptr;
     return LBM_OK;
   }
   const int64_t n = st->sp->n;
   if (!st->alpha) {
-    if (dev_alloc(&st->alpha, compute_bytes(st->precision) * (size_t)(n > 0 ? n : 1),
-                  st->sp->stream, false) != cudaSuccess) {
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    void* afx = nullptr;
+    if (dev_alloc(&st->alpha, compute_bytes(st->precision) * nn, st->sp->stream, false) !=
+            cudaSuccess ||
+        (st->precision == LBM_F64X &&
+         dev_alloc(&afx, 2 * sizeof(int64_t) * nn, st->sp->stream, false) != cudaSuccess)) {
       cudaGetLastError();
+      dev_free(st->alpha, st->sp->stream, false);
       st->alpha = nullptr;
       return fail(LBM_ENOMEM, "damping field allocation failed");
     }
+    st->alpha_fx = (int64_t*)afx;
   }
   if (n > 0) {
     const unsigned grid = (unsigned)((n + 255) / 256);
-    if (st->precision == LBM_F64)
+    if (compute_bytes(st->precision) == 8)   // the FP64 forms, FP64 storage in fixed point included
       set_alpha_kernel<double><<<grid, 256, 0, st->sp->stream>>>((double*)st->alpha, alpha_dev, (int32_t)n);
     else
       set_alpha_kernel<float><<<grid, 256, 0, st->sp->stream>>>((float*)st->alpha, alpha_dev, (int32_t)n);
     LBM_CUDA_TRY(cudaGetLastError());
+    if (st->alpha_fx) {
+      const int rc = set_alpha_fx(st, alpha_dev);
+      if (rc != LBM_OK) return rc;
+    }
   }
   return LBM_OK;
 }

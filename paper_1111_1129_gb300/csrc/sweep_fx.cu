@@ -21,9 +21,17 @@
 //    remainder rho - 1 - sum_{q>0} X*_q (and a diagonal population the last
 //    sub-unit part), so every collision conserves the stored mass exactly.
 //
-// A cell with any PDF outside its range or with |u| >= 2^-6 (fast flow,
-// random test states, NaN) takes the IEEE FP64 collision instead, and an output that leaves its
-// range is written through FP64; both are exact to FP64 round-off.  The
+// Brinkman damping alpha_n stays in fixed point too.  lbm_set_damping stores
+// per cell A = alpha 2^63 and E = e 2^63 with e = (alpha/2) / (1 + alpha/2),
+// so that u = (j + F/2)/(1 + alpha/2) = (j + F/2) - e (j + F/2), and the
+// odd-part coefficient w-/6 - b1 alpha (b1 = (1 - w-/2)/6) is an integer
+// product of two 63-bit constants: the damped step issues no FP64
+// instruction either, and reads 16 bytes more per update.
+//
+// A cell with any PDF outside its range, with |u| >= 2^-6 (fast flow,
+// random test states, NaN) or with alpha outside [0, 1/2) takes the IEEE
+// FP64 collision instead, and an output that leaves its range is written
+// through FP64; both are exact to FP64 round-off.  The
 // update is the TRT update of the FP64 form (same pair formulation), with
 // errors below FP64 round-off of f.
 #include "lbm_kernels.cuh"
@@ -38,6 +46,7 @@ struct FxCoef {
   int64_t q1;               // w+/36 (quadratic terms) * 2^63
   int64_t hF[3];            // F/2 in units U
   int64_t bF1[3];           // (1 - w-/2) F / 6 in units U
+  int64_t b1x2;             // 2 (1 - w-/2)/6 * 2^63: mul.hi with alpha 2^63 gives b1 alpha 2^63
 };
 
 // (a * b) / 2^58 for |a|, |b| < 2^52, from three 32x32 -> 64 products:
@@ -151,11 +160,12 @@ __device__ __forceinline__ bool fx_moments(const int64_t b[19], const FxCoef& k,
 template <bool HP_POW2>
 __device__ __forceinline__ void fx_collide_store(const int64_t S[9], const int64_t D[9],
                                                  int64_t drho, int64_t ux, int64_t uy,
-                                                 int64_t uz, const FxCoef& k,
+                                                 int64_t uz, const FxCoef& k, int64_t a1,
                                                  double* __restrict__ dst, int32_t n, int32_t i) {
-  const int64_t V1x = fxmul(ux, k.a1) + k.bF1[0];
-  const int64_t V1y = fxmul(uy, k.a1) + k.bF1[1];
-  const int64_t V1z = fxmul(uz, k.a1) + k.bF1[2];
+  // a1: the odd-part coefficient w-/6 (undamped) or w-/6 - b1 alpha, * 2^63
+  const int64_t V1x = fxmul(ux, a1) + k.bF1[0];
+  const int64_t V1y = fxmul(uy, a1) + k.bF1[1];
+  const int64_t V1z = fxmul(uz, a1) + k.bF1[2];
   const int64_t V2x = V1x >> 1, V2y = V1y >> 1, V2z = V1z >> 1;
   // Quadratic terms w+ w_p (4.5 (c.u)^2 - 1.5 u.u) = (w+ w_p / 2)
   // (9 (c.u)^2 - 3 u.u): with v = (w+/36) u, the products
@@ -223,11 +233,12 @@ __device__ __forceinline__ void fx_collide_store(const int64_t S[9], const int64
 }
 
 // The IEEE FP64 collision of one cell (out-of-range cells) and its store.
+template <bool DAMPED>
 __device__ __forceinline__ void fx_ieee_collide_store(double g[19], const Coef<double>& kd,
-                                                      double* __restrict__ dst, int32_t n,
-                                                      int32_t i, double red[4]) {
+                                                      double alpha, double* __restrict__ dst,
+                                                      int32_t n, int32_t i, double red[4]) {
   double rho, u[3];
-  collide<double, false>(g, kd, 0.0, rho, u);
+  collide<double, DAMPED>(g, kd, alpha, rho, u);
 #pragma unroll
   for (int q = 0; q < 19; ++q) st_cs(dst + q * n + i, g[q]);
   red[0] = rho;
@@ -236,11 +247,32 @@ __device__ __forceinline__ void fx_ieee_collide_store(double g[19], const Coef<d
   red[3] = u[2];
 }
 
+// Damping of cell i in fixed point: u <- u - e u (u = j + F/2 in units U)
+// and the odd-part coefficient w-/6 - b1 alpha (* 2^63).  False if the cell
+// must take the IEEE path (alpha outside [0, 1/2)).
+template <bool DAMPED>
+__device__ __forceinline__ bool fx_damp(const int64_t* __restrict__ alpha_fx, int32_t n,
+                                        int32_t i, const FxCoef& k, int64_t& ux, int64_t& uy,
+                                        int64_t& uz, int64_t& a1) {
+  a1 = k.a1;
+  if constexpr (DAMPED) {
+    const int64_t A = __ldg(alpha_fx + i);
+    if (A < 0) return false;
+    const int64_t E = __ldg(alpha_fx + n + i);
+    ux -= fxmul(ux, E);
+    uy -= fxmul(uy, E);
+    uz -= fxmul(uz, E);
+    a1 -= __mul64hi(k.b1x2, A);
+  }
+  return true;
+}
+
 // A step that does not reduce.
-template <bool HP_POW2>
+template <bool HP_POW2, bool DAMPED>
 __global__ void __launch_bounds__(kSweepThreads, LBM_FX_MIN_BLOCKS)
     sweep_fx_kernel(const double* __restrict__ src, double* __restrict__ dst,
-                    const int32_t* __restrict__ adj, int32_t n, FxCoef k, Coef<double> kd) {
+                    const int32_t* __restrict__ adj, int32_t n, FxCoef k, Coef<double> kd,
+                    const double* __restrict__ alpha, const int64_t* __restrict__ alpha_fx) {
   const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
   prior_step_done();  // a chained launch waits here for the previous step
   if (i < n) {
@@ -248,14 +280,15 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_FX_MIN_BLOCKS)
     int64_t b[19];
     load_links(adj, n, i, idx);
     fx_pull(src, idx, i, b);
-    int64_t S[9], D[9], drho = 0, ux = 0, uy = 0, uz = 0;
-    if (fx_moments(b, k, S, D, drho, ux, uy, uz)) {
-      fx_collide_store<HP_POW2>(S, D, drho, ux, uy, uz, k, dst, n, i);
+    int64_t S[9], D[9], drho = 0, ux = 0, uy = 0, uz = 0, a1 = 0;
+    if (fx_moments(b, k, S, D, drho, ux, uy, uz) &&
+        fx_damp<DAMPED>(alpha_fx, n, i, k, ux, uy, uz, a1)) {
+      fx_collide_store<HP_POW2>(S, D, drho, ux, uy, uz, k, a1, dst, n, i);
     } else {
       double g[19], red[4];
 #pragma unroll
       for (int q = 0; q < 19; ++q) g[q] = __longlong_as_double(b[q]);
-      fx_ieee_collide_store(g, kd, dst, n, i, red);
+      fx_ieee_collide_store<DAMPED>(g, kd, DAMPED ? ld_nc(alpha + i) : 0.0, dst, n, i, red);
     }
   }
 }
@@ -265,35 +298,37 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_FX_MIN_BLOCKS)
 // rather than keep the raw bits live: the reduction then adds little to the
 // registers the collision needs.  (Sharing this structure with the plain
 // step made that one spill.)
-template <bool HP_POW2>
+template <bool HP_POW2, bool DAMPED>
 __global__ void __launch_bounds__(kSweepThreads, LBM_FX_RED_MIN_BLOCKS)
     sweep_fx_reduce_kernel(const double* __restrict__ src, double* __restrict__ dst,
                            const int32_t* __restrict__ adj, int32_t n, FxCoef k,
-                           Coef<double> kd, double* __restrict__ partials) {
+                           Coef<double> kd, const double* __restrict__ alpha,
+                           const int64_t* __restrict__ alpha_fx, double* __restrict__ partials) {
   const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
   const bool live = i < n;
   bool fast = false;
-  int64_t S[9], D[9], drho = 0, ux = 0, uy = 0, uz = 0;
+  int64_t S[9], D[9], drho = 0, ux = 0, uy = 0, uz = 0, a1 = 0;
   const int32_t z = prior_step_done();  // zero, after the previous step has finished
   if (live) {
     int32_t idx[18];
     int64_t b[19];
     load_links(adj, n, i, idx);
     fx_pull(src, idx, i, b);
-    fast = fx_moments(b, k, S, D, drho, ux, uy, uz);
+    fast = fx_moments(b, k, S, D, drho, ux, uy, uz) &&
+           fx_damp<DAMPED>(alpha_fx, n, i, k, ux, uy, uz, a1);
   }
   fast ? fx_fixed_warp_sums(drho, ux, uy, uz, 1, partials + z)
        : fx_fixed_warp_sums(0, 0, 0, 0, 0, partials + z);
   double red[4] = {0.0, 0.0, 0.0, 0.0};   // IEEE-path cells: rho, u
   if (live) {
     if (fast) {
-      fx_collide_store<HP_POW2>(S, D, drho, ux, uy, uz, k, dst, n, i);
+      fx_collide_store<HP_POW2>(S, D, drho, ux, uy, uz, k, a1, dst, n, i);
     } else {
       double g[19];
       g[0] = ld_nc(src + i);
 #pragma unroll
       for (int q = 1; q < 19; ++q) g[q] = ld_nc(src + __ldg(adj + (q - 1) * n + i));
-      fx_ieee_collide_store(g, kd, dst, n, i, red);
+      fx_ieee_collide_store<DAMPED>(g, kd, DAMPED ? ld_nc(alpha + i) : 0.0, dst, n, i, red);
     }
   }
   fx_ieee_warp_add(red, live && !fast, partials + z);
@@ -304,17 +339,19 @@ int64_t units(double v) { return (int64_t)std::llround(v * 0x1p58); }
 
 }  // namespace
 
-int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3],
-                    cudaStream_t stream, bool reduce_last) {
-  const int32_t n = (int32_t)st->sp->n;
+namespace {
+
+// Fixed-point coefficients of a step with these rates and force; *pow2:
+// (1 - w+)/2 is an exact power of two, so the even-part products are shifts.
+FxCoef make_fx_coef(double wp, double wm, const double F[3], bool* pow2) {
   FxCoef k{};
   k.hp = c63(0.5 * (1.0 - wp));
   // exact power of two (the mantissa of |hp| is 1/2) between 2^-1 and 2^-40
   const double hp = 0.5 * (1.0 - wp);
   int e = 0;
   const double m = hp != 0.0 ? std::frexp(std::fabs(hp), &e) : 0.0;
-  const bool pow2 = m == 0.5 && -e + 1 >= 1 && -e + 1 <= 40;
-  k.hp_shift = pow2 ? 1 - e : 0;
+  *pow2 = m == 0.5 && -e + 1 >= 1 && -e + 1 <= 40;
+  k.hp_shift = *pow2 ? 1 - e : 0;
   k.hp_sign = hp < 0 ? -1 : 1;
   k.hm = c63(0.5 * (1.0 - wm));
   k.w1p = c63(wp / 18.0);
@@ -324,23 +361,83 @@ int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const 
     k.bF1[d] = units((1.0 - 0.5 * wm) * F[d] / 6.0);
   }
   k.q1 = c63(wp / 36.0);
-  const Coef<double> kd = make_coef<double>(wp, wm, F, 0);
+  k.b1x2 = 2 * c63((1.0 - 0.5 * wm) / 6.0);
+  return k;
+}
+
+// One fixed-point step of state st from src to dst (its damping included);
+// partials non-null: the reducing variant.
+cudaError_t launch_fx(const lbm_state* st, const double* src, double* dst, const FxCoef& k,
+                      bool pow2, const Coef<double>& kd, cudaStream_t stream, bool chained,
+                      double* partials) {
+  const int32_t n = (int32_t)st->sp->n;
   const unsigned grid = (unsigned)st->nblocks;
+  const int32_t* adj = st->sp->adj;
+  const double* alpha = (const double*)st->alpha;
+  const int64_t* afx = st->alpha_fx;
+#define LBM_FX_LAUNCH(P2, DA)                                                                       \
+  return partials ? launch_sweep(sweep_fx_reduce_kernel<P2, DA>, grid, stream, chained, src, dst, adj, n, k, kd, alpha, afx, partials) \
+                  : launch_sweep(sweep_fx_kernel<P2, DA>, grid, stream, chained, src, dst, adj, n, k, kd, alpha, afx)
+  if (alpha) {
+    if (pow2) LBM_FX_LAUNCH(true, true);
+    LBM_FX_LAUNCH(false, true);
+  }
+  if (pow2) LBM_FX_LAUNCH(true, false);
+  LBM_FX_LAUNCH(false, false);
+#undef LBM_FX_LAUNCH
+}
+
+}  // namespace
+
+int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const double F[3],
+                    cudaStream_t stream, bool reduce_last) {
+  bool pow2 = false;
+  const FxCoef k = make_fx_coef(wp, wm, F, &pow2);
+  const Coef<double> kd = make_coef<double>(wp, wm, F, 0);
   for (int32_t t = 0; t < n_steps; ++t) {
     const double* src = (const double*)st->buf[st->cur];
     double* dst = (double*)st->buf[st->cur ^ 1];
-    if (n > 0) {
-      const int32_t* adj = st->sp->adj;
-      const bool chained = t > 0;
-      if (reduce_last && t == n_steps - 1)
-        LBM_CUDA_TRY(pow2 ? launch_sweep(sweep_fx_reduce_kernel<true>, grid, stream, chained, src, dst, adj, n, k, kd, st->partials)
-                          : launch_sweep(sweep_fx_reduce_kernel<false>, grid, stream, chained, src, dst, adj, n, k, kd, st->partials));
-      else
-        LBM_CUDA_TRY(pow2 ? launch_sweep(sweep_fx_kernel<true>, grid, stream, chained, src, dst, adj, n, k, kd)
-                          : launch_sweep(sweep_fx_kernel<false>, grid, stream, chained, src, dst, adj, n, k, kd));
+    if (st->sp->n > 0) {
+      const bool last = reduce_last && t == n_steps - 1;
+      LBM_CUDA_TRY(launch_fx(st, src, dst, k, pow2, kd, stream, t > 0, last ? st->partials : nullptr));
     }
     st->cur ^= 1;
   }
+  return LBM_OK;
+}
+
+int launch_fx_step(const lbm_state* st, const double* src, double* dst, double wp, double wm,
+                   const double F[3], cudaStream_t stream, bool chained) {
+  if (st->sp->n == 0) return LBM_OK;
+  bool pow2 = false;
+  const FxCoef k = make_fx_coef(wp, wm, F, &pow2);
+  const Coef<double> kd = make_coef<double>(wp, wm, F, 0);
+  LBM_CUDA_TRY(launch_fx(st, src, dst, k, pow2, kd, stream, chained, nullptr));
+  return LBM_OK;
+}
+
+namespace {
+// alpha_fx of a damped FP64-storage state: A = alpha 2^63 (or -1 where alpha
+// is outside [0, 1/2): that cell takes the IEEE path) and
+// E = e 2^63, e = (alpha/2) / (1 + alpha/2).
+__global__ void set_alpha_fx_kernel(const double* __restrict__ a, int32_t n,
+                                    int64_t* __restrict__ out) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double al = a[i];
+  const bool ok = al >= 0.0 && al < 0.5;
+  const double e = ok ? (0.5 * al) / (1.0 + 0.5 * al) : 0.0;
+  out[i] = ok ? (int64_t)llrint(al * 0x1p63) : -1;
+  out[n + i] = ok ? (int64_t)llrint(e * 0x1p63) : 0;
+}
+}  // namespace
+
+int set_alpha_fx(lbm_state* st, const double* alpha_dev) {
+  const int64_t n = st->sp->n;
+  if (n == 0) return LBM_OK;
+  set_alpha_fx_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st->sp->stream>>>(
+      alpha_dev, (int32_t)n, st->alpha_fx);
+  LBM_CUDA_TRY(cudaGetLastError());
   return LBM_OK;
 }
 

@@ -40,10 +40,13 @@ def _setup(flags, periodic, precision="f64", alpha_dense=None, f0_dense=None, or
     return lat, st, cells
 
 
+@pytest.mark.parametrize("precision", ["f64", "f64x"])
 @pytest.mark.parametrize("shape,periodic,K,stride", [
     ((4, 5, 6), 0b100, 1, 0), ((4, 5, 6), 0b100, 6, 2), ((5, 4, 3), 0b011, 9, 0),
     ((3, 3, 3), 0b111, 5, 1), ((6, 4, 5), 0b000, 12, 5), ((2, 7, 4), 0b010, 7, 7)])
-def test_fp64_adjoint_matches_oracle_adjoint(shape, periodic, K, stride):
+def test_fp64_adjoint_matches_oracle_adjoint(shape, periodic, K, stride, precision):
+    """FP64 arithmetic (IEEE) and FP64 storage whose steps run in fixed
+    point, damped, against the oracle's explicit-Jacobian adjoint."""
     rng = np.random.default_rng(sum(shape) * 31 + K)
     flags = (rng.random(shape) < 0.25).astype(np.uint8)
     alpha = 0.05 * rng.random(shape)
@@ -52,7 +55,7 @@ def test_fp64_adjoint_matches_oracle_adjoint(shape, periodic, K, stride):
     axis = 2
     J_ref, dF_ref, da_ref, lam0_ref = oracle.adjoint(flags, periodic, WP, WM, F, K, axis,
                                                      alpha=alpha, f0=f0)
-    lat, st, cells = _setup(flags, periodic, alpha_dense=alpha, f0_dense=f0)
+    lat, st, cells = _setup(flags, periodic, precision, alpha_dense=alpha, f0_dense=f0)
     adj = Adjoint(st, K, stride)
     J = adj.forward(WP, WM, F, axis)
     dF, da, df0 = adj.backward(want_alpha=True, want_f0=True)
@@ -69,10 +72,12 @@ def test_fp64_adjoint_matches_oracle_adjoint(shape, periodic, K, stride):
     lat.close()
 
 
-def test_checkpoint_stride_does_not_change_the_result():
+@pytest.mark.parametrize("precision", ["f64", "f64x", "f32s"])
+def test_checkpoint_stride_does_not_change_the_result(precision):
     bed = inputs.packed_bed((20, 18, 24), 2, 16.0, 3.0, 0.45, 3)
     alpha = inputs.alpha_field(bed.dims, seed=3)
-    lat, st, _ = _setup(bed.flags, bed.periodic, alpha_dense=alpha, ordering="morton1")
+    lat, st, _ = _setup(bed.flags, bed.periodic, precision, alpha_dense=alpha,
+                        ordering="morton1")
     ref = None
     for stride in (1, 3, 7, 30, 40):
         adj = Adjoint(st, 40, stride)

@@ -45,11 +45,13 @@ def _rel(a, b):
     return np.max(np.abs(a - b)) / np.max(np.abs(b))
 
 
+@pytest.mark.parametrize("precision", ["f64", "f64x"])
 @pytest.mark.parametrize("shape", [(2, 2, 2), (3, 4, 5), (6, 6, 6), (5, 1, 3)])
 @pytest.mark.parametrize("periodic", range(8))
-def test_tiny_boxes_random_state_parity(shape, periodic):
+def test_tiny_boxes_random_state_parity(shape, periodic, precision):
     """Brute force on tiny boxes: random flags, random initial PDFs, random
-    damping, 1-10 steps, every periodicity mask."""
+    damping, 1-10 steps, every periodicity mask; IEEE FP64 and FP64 storage
+    in fixed point."""
     rng = np.random.default_rng(hash((shape, periodic)) % 2**32)
     flags = (rng.random(shape) < 0.25).astype(np.uint8)
     if (flags == 0).sum() == 0:
@@ -58,14 +60,15 @@ def test_tiny_boxes_random_state_parity(shape, periodic):
     alpha = 0.05 * rng.random(shape)
     F = 1e-3 * rng.standard_normal(3)
     for steps in (1, 3, 10):
-        lat, st, cells = _gpu_run(flags, periodic, steps, F, alpha_dense=alpha, f0_dense=f0)
+        lat, st, cells = _gpu_run(flags, periodic, steps, F, precision=precision,
+                                  alpha_dense=alpha, f0_dense=f0)
         f_ref, obs, rho_ref, u_ref = oracle.run(flags, periodic, WP, WM, F, steps, alpha=alpha,
                                                 f=f0)
         got = st.get_pdfs().cpu().numpy()
         rho, u = st.moments()
         fp64_measures.check(got, oracle.to_sparse(f_ref, cells), steps, u.cpu().numpy(),
                             oracle.to_sparse(u_ref, cells),
-                            label=f"tiny box {shape} periodic {periodic}")
+                            label=f"tiny box {shape} periodic {periodic} {precision}")
         np.testing.assert_allclose(rho.cpu().numpy(), oracle.to_sparse(rho_ref, cells),
                                    rtol=0, atol=1e-13)
         np.testing.assert_allclose(u.cpu().numpy(), oracle.to_sparse(u_ref, cells), rtol=0,
@@ -143,16 +146,18 @@ def test_orderings_give_bitwise_identical_fields():
         lat.close()
 
 
-def test_damped_bed_parity():
+@pytest.mark.parametrize("precision", ["f64", "f64x"])
+def test_damped_bed_parity(precision):
     bed = inputs.packed_bed((24, 20, 28), 2, 18.0, 3.0, 0.45, 5)
     alpha = inputs.alpha_field(bed.dims, seed=5)
     F = (0.0, 0.0, 1e-5)
-    lat, st, cells = _gpu_run(bed.flags, bed.periodic, 200, F, "morton1", alpha_dense=alpha)
+    lat, st, cells = _gpu_run(bed.flags, bed.periodic, 200, F, "morton1", precision=precision,
+                              alpha_dense=alpha)
     f_ref, obs, _, u_ref = oracle.run(bed.flags, bed.periodic, WP, WM, F, 200, alpha=alpha)
     _, u = st.moments()
     m = fp64_measures.check(st.get_pdfs().cpu().numpy(), oracle.to_sparse(f_ref, cells), 200,
                             u.cpu().numpy(), oracle.to_sparse(u_ref, cells),
-                            label="damped bed, 200 steps")
+                            label=f"damped bed, 200 steps, {precision}")
     mass, flux = st.reduce_flux(2)
     assert abs(flux - obs[-1, 3] / bed.n_fluid) <= m["bound_abs_du"] + 2.0 ** -61
     st.close()
