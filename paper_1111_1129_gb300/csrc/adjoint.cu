@@ -287,12 +287,17 @@ __host__ __device__ __forceinline__ ds ds_from_double(double v) {
   return {hi, (float)(v - (double)hi)};
 }
 // An int64 value in units 2^-sc (sc = 58 or 63, |v| < 2^62), to ~48 bits.
+// 64-bit integer conversions issue at the FP64 rate on GB300, so v is cut
+// into three 21-bit pieces, each converted exactly as a 32-bit integer, and
+// the pieces are summed as pairs.
 __device__ __forceinline__ ds ds_from_fixed(int64_t v, int sc) {
-  const float hi = (float)v;   // round to nearest
-  const int64_t rest = v - (int64_t)hi;
-  const float lo = (float)rest;
+  const float a = (float)(int32_t)(v >> 42) * 0x1p42f;                 // exact
+  const float b = (float)(int32_t)((v >> 21) & 0x1FFFFF) * 0x1p21f;    // exact
+  const float c = (float)(int32_t)(v & 0x1FFFFF);                      // exact
+  const ds ab = ds_two_sum(a, b);
+  const ds r = ds_add(ab, ds{c, 0.f});
   const float scale = sc == 58 ? 0x1p-58f : 0x1p-63f;   // exact: powers of two
-  return {hi * scale, lo * scale};
+  return {r.hi * scale, r.lo * scale};
 }
 
 // Coefficients of the reverse step as pairs.
