@@ -436,8 +436,13 @@ __global__ void __launch_bounds__(kSweepThreads)
 
 // One reverse step of the FP64-storage adjoint (adjoint_step_kernel's
 // formulas) in double-single arithmetic.
+#ifdef LBM_ADJ_DS_MIN_BLOCKS
+#define LBM_ADJ_DS_BOUNDS __launch_bounds__(kSweepThreads, LBM_ADJ_DS_MIN_BLOCKS)
+#else
+#define LBM_ADJ_DS_BOUNDS __launch_bounds__(kSweepThreads)
+#endif
 template <bool DAMPED>
-__global__ void __launch_bounds__(kSweepThreads)
+__global__ void LBM_ADJ_DS_BOUNDS
     adjoint_step_ds_kernel(const double* __restrict__ f_prev, const int32_t* __restrict__ adj,
                            int32_t n, Coef<double> kd, AdjCoefDS a,
                            const double* __restrict__ alpha, const int64_t* __restrict__ alpha_fx,
