@@ -72,6 +72,34 @@ def test_fp64_adjoint_matches_oracle_adjoint(shape, periodic, K, stride, precisi
     lat.close()
 
 
+@pytest.mark.parametrize("precision", ["f64", "f64x"])
+def test_fp64_adjoint_with_strong_damping_matches_oracle(precision):
+    """Damping drawn in [0, 1]: the FP64-storage form's cells with
+    alpha >= 1/2 take the IEEE paths of the fixed-point sweep and of the
+    double-single reverse step, the others the fast paths."""
+    rng = np.random.default_rng(77)
+    shape = (6, 5, 7)
+    flags = (rng.random(shape) < 0.2).astype(np.uint8)
+    alpha = rng.random(shape)
+    F = np.array([2e-4, 1e-4, -5e-4])
+    f0 = oracle.rest_state(flags) * (1 + 0.005 * rng.standard_normal((19,) + shape))
+    K, axis = 8, 0
+    J_ref, dF_ref, da_ref, lam0_ref = oracle.adjoint(flags, 0b001, WP, WM, F, K, axis,
+                                                     alpha=alpha, f0=f0)
+    lat, st, cells = _setup(flags, 0b001, precision, alpha_dense=alpha, f0_dense=f0)
+    assert (oracle.to_sparse(alpha, cells) >= 0.5).any()
+    adj = Adjoint(st, K, 3)
+    J = adj.forward(WP, WM, F, axis)
+    dF, da, df0 = adj.backward(want_alpha=True, want_f0=True)
+    assert abs(J - J_ref) <= 1e-12 * abs(J_ref)
+    assert _norm_rel(dF, dF_ref) <= 1e-10
+    assert _norm_rel(da.cpu().numpy(), oracle.to_sparse(da_ref, cells)) <= 1e-10
+    assert _norm_rel(df0.cpu().numpy(), oracle.to_sparse(lam0_ref, cells)) <= 1e-10
+    adj.close()
+    st.close()
+    lat.close()
+
+
 @pytest.mark.parametrize("precision", ["f64", "f64x", "f32s"])
 def test_checkpoint_stride_does_not_change_the_result(precision):
     bed = inputs.packed_bed((20, 18, 24), 2, 16.0, 3.0, 0.45, 3)

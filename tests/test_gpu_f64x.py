@@ -138,3 +138,28 @@ def test_large_bed_sampled_parity():
     fp64_measures.check(nxt[:, sample], ref, 1, label="f64x large bed, one step, 2000 cells")
     st.close()
     lat.close()
+
+
+def test_strong_damping_takes_the_ieee_path_where_needed():
+    """Damping drawn in [0, 1] on a random-flag box near rest: cells with
+    alpha >= 1/2 take the IEEE collision, the others the fixed-point one;
+    both match the oracle within the FP64 tolerance."""
+    rng = np.random.default_rng(31)
+    shape = (10, 9, 12)
+    flags = (rng.random(shape) < 0.2).astype(np.uint8)
+    alpha = rng.random(shape)
+    f0 = oracle.rest_state(flags) * (1 + 1e-4 * rng.standard_normal((19,) + shape))
+    F = (1e-5, -2e-5, 3e-5)
+    lat = SparseLattice(torch.from_numpy(flags).cuda(), "lex", periodic=0b110)
+    cells = lat.cells().cpu().numpy()
+    st = LBMState(lat, "f64x")
+    st.set_pdfs(torch.from_numpy(oracle.to_sparse(f0, cells).copy()))
+    st.set_damping(torch.from_numpy(alpha.reshape(-1)[cells].copy()))
+    st.step(15, WP, WM, F)
+    f_ref, obs, _, u_ref = oracle.run(flags, 0b110, WP, WM, F, 15, alpha=alpha, f=f0)
+    _, u = st.moments()
+    fp64_measures.check(st.get_pdfs().cpu().numpy(), oracle.to_sparse(f_ref, cells), 15,
+                        u.cpu().numpy(), oracle.to_sparse(u_ref, cells),
+                        label="f64x strong damping")
+    st.close()
+    lat.close()
