@@ -41,9 +41,11 @@
  * Handles (lbm_sparse, lbm_state) own device memory, taken from the
  * caller's allocator if one is set (lbm_set_allocator); they are released by
  * lbm_free.  A state refers to the sparse representation it was created
- * from, which must outlive it.  All work is queued on the stream given to
- * lbm_build_sparse (a cudaStream_t passed as void*, NULL = legacy default
- * stream); functions that return host values synchronise that stream.
+ * from, which must outlive every use of the state; lbm_free may release the
+ * two in either order (a garbage collector may).  All work is queued on the
+ * stream given to lbm_build_sparse (a cudaStream_t passed as void*, NULL =
+ * legacy default stream); functions that return host values synchronise
+ * that stream.
  */
 #ifndef LBM_GB300_H
 #define LBM_GB300_H
@@ -96,8 +98,10 @@ typedef struct lbm_ordering {
 #define LBM_BF16S 4 /* (f - w_q) * 2^k in BF16, FP32 arithmetic */
 #define LBM_F64X 5  /* f in FP64; the sweep computes f - w_q exactly in 64-bit
                        fixed point (unit 2^-58) instead of FP64 instructions,
-                       conserves mass exactly and agrees with LBM_F64 to FP64
-                       round-off; other operations run as LBM_F64 */
+                       damping included, conserves mass exactly and agrees
+                       with LBM_F64 to FP64 round-off; its adjoint steps in
+                       fixed point and reverses in double-single arithmetic
+                       (~48 bits); other operations run as LBM_F64 */
 
 typedef struct lbm_sparse lbm_sparse;
 typedef struct lbm_state lbm_state;
@@ -167,7 +171,12 @@ int lbm_state_reset(lbm_state* st);
 
 /*
  * Per-cell Brinkman damping alpha_n >= 0 in fluid order (device FP64[N]),
- * copied into the state in its arithmetic precision; NULL removes damping.
+ * copied into the state in its arithmetic precision (FP64 for LBM_F64 and
+ * LBM_F64X, FP32 otherwise); NULL removes damping.  An LBM_F64X state also
+ * keeps alpha 2^63 and e 2^63, e = (alpha/2)/(1 + alpha/2), per cell (16
+ * more bytes per cell), so that its fixed-point steps and its adjoint take
+ * damped cells without FP64 arithmetic; cells with alpha outside [0, 1/2)
+ * take the IEEE FP64 update, with the same results to FP64 round-off.
  */
 int lbm_set_damping(lbm_state* st, const double* alpha_dev);
 
@@ -348,12 +357,16 @@ int lbm_halo_gather(const void* src_dev, const int64_t* slots_dev, int64_t count
  * states are kept as checkpoints every `stride` steps in the state's
  * storage form and recomputed between checkpoints (memory ~ (K/stride +
  * stride) states).  Adjoint arithmetic runs in the state's arithmetic
- * precision (FP64 for LBM_F64, FP32 otherwise); sums in FP64.
+ * precision: FP64 for LBM_F64; for LBM_F64X fixed-point forward steps and
+ * double-single reverse steps (lambda as pairs of FP32 values, ~48
+ * significant bits, results within 1e-10 of FP64); FP32 otherwise.  Sums in
+ * FP64.
  */
 typedef struct lbm_adjoint lbm_adjoint;
 
 /* Buffers for K = n_steps >= 1 steps of state st (its lattice, form and
- * damping); stride = 0 picks ceil(sqrt(K)).  The state must outlive it. */
+ * damping); stride = 0 picks ceil(sqrt(K)).  The state must outlive every
+ * forward and backward pass; lbm_free may release the two in either order. */
 int lbm_adjoint_create(const lbm_state* st, int32_t n_steps, int32_t stride, lbm_adjoint** out);
 
 /* Forward pass from the state's current PDFs (the state is not modified):

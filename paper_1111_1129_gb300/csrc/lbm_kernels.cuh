@@ -469,7 +469,9 @@ __device__ __forceinline__ uint32_t c_to_bits(float v, float scale) {
 // runs: 4-byte stores on the other rows too, built with a lane shuffle,
 // 41,923; one 4-byte load for both pulls where they share a word 29,135;
 // 8-byte link loads on the aligned rows 29,844-30,936 (with and without the
-// L2 hint, non-coherent or coherent); link rows through bulk copies into
+// L2 hint, non-coherent or coherent; with registers to spare, 78 at 3 blocks
+// per SM, 25,215 against 41,622 for scalar loads at that occupancy, so not
+// register pressure); link rows through bulk copies into
 // shared memory, completed on an mbarrier 36,780; three or four cells per
 // thread 33,154 / 28,450; cells i and i + 32 of a warp's 64 40,189; links
 // loaded before the wait for the previous step 37,263; write-back stores
