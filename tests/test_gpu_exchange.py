@@ -7,9 +7,9 @@ stepped by lbm_step_f64_noalloc on its local adjacency) before every step
 
 The gathered PDFs must equal the FP64 oracle's run of the unsplit bed within
 the FP64 tolerance, and the unsplit GPU run (lbm_step on an FP64 state) bit
-for bit; the all-reduced mass and flux must match both.  A rank that fails
-between steps is reported on the host.  No kernel waits on another rank:
-the ranks meet only on the host, in gloo.
+for bit, with and without Brinkman damping; the all-reduced mass and flux
+must match both.  A rank that fails between steps is reported on the host.
+No kernel waits on another rank: the ranks meet only on the host, in gloo.
 """
 import datetime
 import os
@@ -38,7 +38,7 @@ def _bed():
     return inputs.packed_bed((20, 18, 24), 2, 17.0, 3.0, 0.45, 11)
 
 
-def _worker(rank, world, port, out_dir, ordering, fail_rank):
+def _worker(rank, world, port, out_dir, ordering, fail_rank, damped=False):
     import torch.distributed as dist
 
     from paper_1111_1129_gb300 import SparseLattice, build, capi, omega_minus
@@ -57,11 +57,18 @@ def _worker(rank, world, port, out_dir, ordering, fail_rank):
         plans, send = plan(lat.adjacency().cpu().numpy(), lat.n, world)
         runner = ChunkRunner(plans[rank], send[rank])
         wm = omega_minus(WP)
-        runner.step(3, WP, wm, F)
+        alpha = None
+        if damped:   # the rank's own cells of the seeded per-box-cell field
+            from paper_1111_1129_gb300 import inputs
+            a_box = inputs.alpha_field(bed.dims, seed=4).reshape(-1)
+            cells = lat.cells().cpu().numpy()
+            me = plans[rank]
+            alpha = torch.from_numpy(a_box[cells[me.begin:me.begin + me.count]].copy()).cuda()
+        runner.step(3, WP, wm, F, alpha)
         if rank == fail_rank:
             torch.cuda.synchronize()     # nothing of this rank in flight
             raise RuntimeError(f"rank {rank} failed on purpose between steps")
-        runner.step(STEPS - 3, WP, wm, F)
+        runner.step(STEPS - 3, WP, wm, F, alpha)
         sums = [runner.reduce_flux(axis, lat.n) for axis in range(3)]
         np.save(os.path.join(out_dir, f"rank{rank}.npy"), runner.pdfs().cpu().numpy())
         if rank == 0:
@@ -71,14 +78,15 @@ def _worker(rank, world, port, out_dir, ordering, fail_rank):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,ordering", [(2, "lex"), (3, "blocked")])
-def test_ranks_reproduce_the_unsplit_run(tmp_path, world, ordering):
+@pytest.mark.parametrize("world,ordering,damped", [(2, "lex", False), (3, "blocked", False),
+                                                   (2, "blocked", True)])
+def test_ranks_reproduce_the_unsplit_run(tmp_path, world, ordering, damped):
     import fp64_measures
     import oracle
     from paper_1111_1129_gb300 import LBMState, SparseLattice, build, capi, omega_minus
     from paper_1111_1129_gb300.partition import chunk_bounds
-    mp.spawn(_worker, args=(world, _free_port(), str(tmp_path), ordering, -1), nprocs=world,
-             join=True)
+    mp.spawn(_worker, args=(world, _free_port(), str(tmp_path), ordering, -1, damped),
+             nprocs=world, join=True)
     build.build()
     capi.load()
     bed = _bed()
@@ -94,14 +102,21 @@ def test_ranks_reproduce_the_unsplit_run(tmp_path, world, ordering):
     kind = {"lex": oracle.ORDER_LEX, "blocked": oracle.ORDER_BLOCKED}[ordering]
     cells, _, _ = oracle.build_sparse(bed.flags, kind, (4, 4, 4), bed.periodic)
     np.testing.assert_array_equal(lat.cells().cpu().numpy(), cells)
-    f_ref, obs, _, _ = oracle.run(bed.flags, bed.periodic, WP, omega_minus(WP), F, STEPS)
+    a_box = None
+    if damped:
+        from paper_1111_1129_gb300 import inputs
+        a_box = inputs.alpha_field(bed.dims, seed=4)
+    f_ref, obs, _, _ = oracle.run(bed.flags, bed.periodic, WP, omega_minus(WP), F, STEPS,
+                                  alpha=a_box)
     m = fp64_measures.check(got, oracle.to_sparse(f_ref, cells), STEPS,
-                            label=f"exchange {world} ranks {ordering}")
+                            label=f"exchange {world} ranks {ordering} damped={damped}")
     assert abs(sums[0][0] - obs[-1, 0]) <= 1e-12 * obs[-1, 0]
     for axis in range(3):
         assert abs(sums[axis][1] - obs[-1, 1 + axis] / n) <= 11 * m["bound_abs_df"] + 2.0 ** -61
     # the unsplit GPU run, bit for bit
     st = LBMState(lat, "f64")
+    if damped:
+        st.set_damping(torch.from_numpy(a_box.reshape(-1)[cells].copy()))
     st.step(STEPS, WP, omega_minus(WP), F)
     np.testing.assert_array_equal(got, st.get_pdfs().cpu().numpy())
     for axis in range(3):
