@@ -129,10 +129,14 @@ int lbm_ordering_keys(const int32_t dims[3], lbm_ordering ord, uint64_t* keys_de
  * out:       receives a library-owned handle holding, in device memory,
  *            cells[N] (box index of the fluid cell with I_c = n + 1, i.e.
  *            fluid cells ranked by key), inv[nx*ny*nz] (n, or -1 for solid)
- *            and adj[18*N] (layout above).
+ *            and adj[18*N] (layout above).  Unless N is a multiple of 64 it
+ *            also holds the same links in the layout the states keep
+ *            internally (rows of L = N rounded up to 64 slots, so that
+ *            every row starts on a 128-byte boundary; 72 bytes per L), which
+ *            the steps read; lbm_sparse_info presents adj only.
  * The call synchronises `stream` (to learn N, and again before returning,
  * so the flags may be released afterwards).  Errors: LBM_EINVAL,
- * LBM_EFLAGS, LBM_EOVERFLOW (19*N >= 2^31), LBM_ENOMEM, LBM_ECUDA.
+ * LBM_EFLAGS, LBM_EOVERFLOW (19*L >= 2^31), LBM_ENOMEM, LBM_ECUDA.
  */
 int lbm_build_sparse(const uint8_t* flags, const int32_t dims[3], lbm_ordering ord,
                      void* stream, lbm_sparse** out);
@@ -147,7 +151,10 @@ int lbm_sparse_info(const lbm_sparse* sp, int64_t* n_fluid, const int32_t** cell
 /*
  * Create a solver state on a sparse representation: two PDF buffers (A/B,
  * pull scheme with swapped grids, Sec. 7) initialised to rest,
- * f_q = w_q (rho0 = 1).
+ * f_q = w_q (rho0 = 1).  Each buffer holds 19 rows of L slots (L = N
+ * rounded up to 64, see lbm_build_sparse); the padding slots are never
+ * read, and every entry point that takes or gives PDFs uses the [19][N]
+ * layout above.
  * precision: LBM_F64 .. LBM_BF16S.
  * scale_exp: k of the 16-bit shifted forms, stored value (f - w_q) * 2^k
  *            rounded to nearest; 0 <= k <= 40; ignored by the other forms.

@@ -609,14 +609,14 @@ struct Runner {
   void step(const S* src, S* dst) const {
     if constexpr (PREC == LBM_F64X) {
       // FP64 storage: the fixed-point sweep, as lbm_step takes it
-      const int rc = launch_fx_step(st, (const double*)src, (double*)dst, ad->wp, ad->wm, ad->F,
-                                    stream, false);
+      const int rc = launch_fx_step(st, (const double*)src, (double*)dst, st->sp->adj, n, ad->wp,
+                                    ad->wm, ad->F, stream, false);
       if (rc != LBM_OK && err == cudaSuccess) err = cudaErrorLaunchFailure;
       chained = true;
       return;
     }
-    if (alpha) launch(sweep_kernel<PREC, true, kNoReduce>, src, dst, st->sp->adj, n, k, alpha, (double*)nullptr);
-    else launch(sweep_kernel<PREC, false, kNoReduce>, src, dst, st->sp->adj, n, k, alpha, (double*)nullptr);
+    if (alpha) launch(sweep_kernel<PREC, true, kNoReduce>, src, dst, st->sp->adj, n, n, k, alpha, (double*)nullptr);
+    else launch(sweep_kernel<PREC, false, kNoReduce>, src, dst, st->sp->adj, n, n, k, alpha, (double*)nullptr);
   }
   void seed(const S* f_prev) const {
     if constexpr (PREC == LBM_F64X) {
@@ -640,10 +640,12 @@ struct Runner {
   }
 
   // Forward pass from the state's current PDFs: checkpoints f_{j*stride};
-  // *last receives where f_{K-1} is.
+  // *last receives where f_{K-1} is.  The adjoint's arrays are [19][N] and
+  // read through the plain links; the state's rows have stride sp->ld.
   int forward(const S** last) const {
-    LBM_CUDA_TRY(cudaMemcpyAsync(ckpt(0), st->buf[st->cur], state_elems * sizeof(S),
-                                 cudaMemcpyDeviceToDevice, stream));
+    LBM_CUDA_TRY(cudaMemcpy2DAsync(ckpt(0), (size_t)n * sizeof(S), st->buf[st->cur],
+                                   (size_t)st->sp->ld * sizeof(S), (size_t)n * sizeof(S), 19,
+                                   cudaMemcpyDeviceToDevice, stream));
     chained = false;
     const S* cur = ckpt(0);
     for (int32_t t = 1; t <= ad->K - 1; ++t) {

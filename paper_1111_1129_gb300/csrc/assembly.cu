@@ -125,10 +125,12 @@ __global__ void __launch_bounds__(kTileThreads)
 }
 
 // Pull adjacency (Sec. 2): source slot of direction i for fluid cell n.
+// adj_ld (or null): the same links in the state layout, rows of ld entries
+// naming slot r ld + m.
 __global__ void adjacency_kernel(int32_t nx, int32_t ny, int32_t nz, uint32_t periodic,
                                  const int32_t* __restrict__ cells,
                                  const int32_t* __restrict__ inv, int32_t* __restrict__ adj,
-                                 int32_t n) {
+                                 int32_t n, int32_t* __restrict__ adj_ld, int32_t ld) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int32_t c = cells[i];
@@ -149,6 +151,7 @@ __global__ void adjacency_kernel(int32_t nx, int32_t ny, int32_t nz, uint32_t pe
     int32_t m = -1;
     if (inside) m = inv[sx + nx * (sy + ny * sz)];
     adj[(q - 1) * n + i] = m >= 0 ? q * n + m : opp(q) * n + i;
+    if (adj_ld) adj_ld[(q - 1) * ld + i] = m >= 0 ? q * ld + m : opp(q) * ld + i;
   }
 }
 
@@ -268,6 +271,7 @@ extern "C" int lbm_build_sparse(const uint8_t* flags, const int32_t dims[3], lbm
       release(sp->cells);
       release(sp->inv);
       release(sp->adj);
+      release(sp->adj_ld);
       delete sp;
     }
     cudaStreamSynchronize(stream);
@@ -304,14 +308,18 @@ extern "C" int lbm_build_sparse(const uint8_t* flags, const int32_t dims[3], lbm
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "sparse assembly: tile count/scan"));
   if (host_scal[1] != 0) return cleanup(fail(LBM_EFLAGS, "flags must be 0 (fluid) or 1 (solid)"));
   const int64_t n = host_scal[0];
-  if (19 * n >= ((int64_t)1 << 31))
+  const int64_t ld = row_stride(n);
+  if (19 * ld >= ((int64_t)1 << 31))
     return cleanup(fail(LBM_EOVERFLOW,
-                        "%lld fluid cells: 19*N PDF slots exceed the int32 adjacency range",
-                        (long long)n));
+                        "%lld fluid cells: 19*L PDF slots (rows of L = %lld, N rounded up to 64) "
+                        "exceed the int32 adjacency range",
+                        (long long)n, (long long)ld));
   sp->n = n;
+  sp->ld = ld;
   const size_t nn = (size_t)(n > 0 ? n : 1);
   if (dev_alloc(&sp->cells, sizeof(int32_t) * nn, stream, true) != cudaSuccess ||
-      dev_alloc(&sp->adj, sizeof(int32_t) * 18 * nn, stream, true) != cudaSuccess) {
+      dev_alloc(&sp->adj, sizeof(int32_t) * 18 * nn, stream, true) != cudaSuccess ||
+      (ld != n && dev_alloc(&sp->adj_ld, sizeof(int32_t) * 18 * (size_t)ld, stream, true) != cudaSuccess)) {
     cudaGetLastError();
     return cleanup(fail(LBM_ENOMEM, "device allocation failed (%lld fluid cells)", (long long)n));
   }
@@ -320,7 +328,8 @@ extern "C" int lbm_build_sparse(const uint8_t* flags, const int32_t dims[3], lbm
   if (n > 0) {
     const int threads = 256;
     adjacency_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, stream>>>(
-        dims[0], dims[1], dims[2], ord.periodic, sp->cells, sp->inv, sp->adj, (int32_t)n);
+        dims[0], dims[1], dims[2], ord.periodic, sp->cells, sp->inv, sp->adj, (int32_t)n,
+        sp->adj_ld, (int32_t)ld);
   }
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);

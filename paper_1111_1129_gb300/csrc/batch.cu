@@ -622,6 +622,7 @@ extern "C" int lbm_state_create_batched(const lbm_sparse* const* beds, int32_t n
   lbm_sparse* cat = new lbm_sparse{};
   cat->magic = kMagicSparse;
   cat->n = total;
+  cat->ld = total;   // a multiple of kBatchChunk: rows already aligned
   cat->stream = stream;
   cat->ord.kind = -1;
   if (dev_alloc(&cat->adj, sizeof(int32_t) * 18 * (size_t)(total > 0 ? total : 1), stream,

@@ -68,7 +68,8 @@ void clear_error() { g_last_error.clear(); }
 void free_sparse(lbm_sparse* sp) {
   if (!sp) return;
   const cudaStream_t s = sp->stream;
-  for (void* p : {(void*)sp->cells, (void*)sp->inv, (void*)sp->adj}) dev_free(p, s, true);
+  for (void* p : {(void*)sp->cells, (void*)sp->inv, (void*)sp->adj, (void*)sp->adj_ld})
+    dev_free(p, s, true);
   cudaStreamSynchronize(s);
   sp->magic = 0;
   delete sp;

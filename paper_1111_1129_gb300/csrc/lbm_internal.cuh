@@ -242,14 +242,34 @@ struct lbm_sparse {
   int64_t n;
   int32_t* cells;  // [n]
   int32_t* inv;    // [box]
-  int32_t* adj;    // [18 * n]
+  int32_t* adj;    // [18 * n], source slot q n + m (the layout lbm_sparse_info presents)
+  // Row stride of the state arrays: n rounded up to kRowAlign (a batch: its
+  // padded total).  adj_ld holds the links in that layout, rows of ld
+  // entries naming slot r ld + m; null when ld == n (adj serves).
+  int64_t ld;
+  int32_t* adj_ld;
   cudaStream_t stream;
 };
+
+namespace lbm {
+// Every row of a state's PDF grids, and of the links its sweeps read, starts
+// on a 128-byte boundary: rows of kRowAlign elements.  On the 1024x256x256
+// bed, a list of a multiple of 64 cells (fluid cells made solid) against the
+// odd list of the same bed, MFLUP/s: FP16 45,537 / 43,390, FP32 31,502 /
+// 30,742, FP64 storage 18,314 / 18,076 (an even list: 45,124 / 31,404 /
+// 18,276).  Misaligned rows cost the 2-byte forms their paired 4-byte stores
+// on every other row, and every form's warp accesses straddle one more line.
+constexpr int64_t kRowAlign = 64;
+inline int64_t row_stride(int64_t n) { return (n + kRowAlign - 1) / kRowAlign * kRowAlign; }
+// The links the sweeps of a state on sp read: rows of sp->ld entries.
+inline const int32_t* state_links(const lbm_sparse* sp) { return sp->adj_ld ? sp->adj_ld : sp->adj; }
+}  // namespace lbm
 
 namespace lbm {
 // Batched state: beds concatenated, each padded to kBatchChunk cells so that
 // every tile of every launch configuration lies inside one bed.
 constexpr int64_t kBatchChunk = 2048;
+static_assert(kBatchChunk % kRowAlign == 0, "a batch's padded rows stay aligned");
 struct Batch {
   int32_t n_beds;
   int64_t* h_begin;      // [n_beds] first padded-list index of each bed (host)
@@ -332,7 +352,7 @@ struct lbm_state {
   cudaStream_t stream;   // sp's stream, kept so that releasing the state needs no sp
   int32_t precision;
   int32_t scale_exp;
-  void* buf[2];        // PDF grids, [19 * n] elements of the storage type
+  void* buf[2];        // PDF grids, 19 rows of sp->ld elements of the storage type (n used)
   int cur;             // index of the grid holding the current PDFs
   void* alpha;         // [n] damping in the arithmetic precision, or nullptr
   int64_t* alpha_fx;   // LBM_F64X with damping: [2][n] alpha 2^63 (-1: the cell takes the
@@ -361,10 +381,12 @@ size_t compute_bytes(int prec);   // bytes of the arithmetic type of a form
 bool is_shifted(int prec);        // stores f - w_q rather than f
 // Fixed-point FP64-storage sweep (sweep_fx.cu), undamped: n_steps launches
 // on `stream`; the last one writes the warp sums when reduce_last is set.
-// One fixed-point step of FP64-storage state st from src to dst (not
-// reducing), queued on `stream`.
-int launch_fx_step(const lbm_state* st, const double* src, double* dst, double wp, double wm,
-                   const double F[3], cudaStream_t stream, bool chained);
+// One fixed-point step of FP64-storage state st (its damping) from src to
+// dst, arrays of rows of stride ld read through links adj (not reducing),
+// queued on `stream`.
+int launch_fx_step(const lbm_state* st, const double* src, double* dst, const int32_t* adj,
+                   int32_t ld, double wp, double wm, const double F[3], cudaStream_t stream,
+                   bool chained);
 // Fills the fixed-point damping rows (alpha_fx) of an FP64-storage state
 // from FP64 alpha on the device.
 int set_alpha_fx(lbm_state* st, const double* alpha_dev);

@@ -328,11 +328,12 @@ __device__ __forceinline__ void store_block_sums(const double w[4], double* out)
   }
 }
 
-// The 18 adjacency entries of cell i (the source slot of each pulled q > 0).
-__device__ __forceinline__ void load_links(const int32_t* __restrict__ adj, int32_t n, int32_t i,
+// The 18 adjacency entries of cell i (the source slot of each pulled q > 0)
+// from link rows of stride ld.
+__device__ __forceinline__ void load_links(const int32_t* __restrict__ adj, int32_t ld, int32_t i,
                                            int32_t idx[18]) {
 #pragma unroll
-  for (int q = 0; q < 18; ++q) idx[q] = ld_nc(adj + q * n + i);
+  for (int q = 0; q < 18; ++q) idx[q] = ld_nc(adj + q * ld + i);
 }
 
 // The 19 pulled values of cell i, given its adjacency entries.
@@ -346,14 +347,14 @@ __device__ __forceinline__ void pull(const typename Form<PREC>::S* __restrict__ 
   for (int q = 1; q < 19; ++q) g[q] = decode<PREC>(load_ro<PREC>(src + idx[q - 1]), inv_scale);
 }
 
-// Gathers the 19 pulled values of cell i.
+// Gathers the 19 pulled values of cell i (link rows of stride ld).
 template <int PREC>
 __device__ __forceinline__ void gather(const typename Form<PREC>::S* __restrict__ src,
-                                       const int32_t* __restrict__ adj, int32_t n, int32_t i,
+                                       const int32_t* __restrict__ adj, int32_t ld, int32_t i,
                                        typename Form<PREC>::C inv_scale,
                                        typename Form<PREC>::C g[19]) {
   int32_t idx[18];
-  load_links(adj, n, i, idx);
+  load_links(adj, ld, i, idx);
   pull<PREC>(src, idx, i, inv_scale, g);
 }
 
@@ -409,6 +410,8 @@ constexpr int sweep_launch_min_blocks() {
                                                                  : sweep_min_blocks<PREC>();
 }
 
+// n cells; the PDF rows of src and dst and the link rows of adj have stride
+// ld >= n, and the links name slots r ld + m.
 // LINKS_FIRST: load the adjacency entries before waiting for the previous
 // step (a chained launch then overlaps them with that step's end), instead of
 // after.  On a grid of one wave (the 32x32x64 bed) that made the FP32 and
@@ -418,7 +421,7 @@ template <int PREC, bool DAMPED, int RED, bool LINKS_FIRST = false>
 __global__ void __launch_bounds__(kSweepThreads, sweep_launch_min_blocks<PREC, RED>())
     sweep_kernel(const typename Form<PREC>::S* __restrict__ src,
                  typename Form<PREC>::S* __restrict__ dst, const int32_t* __restrict__ adj,
-                 int32_t n, Coef<typename Form<PREC>::C> k,
+                 int32_t n, int32_t ld, Coef<typename Form<PREC>::C> k,
                  const typename Form<PREC>::C* __restrict__ alpha, double* __restrict__ partials) {
   using C = typename Form<PREC>::C;
   const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
@@ -426,14 +429,14 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_launch_min_blocks<PREC, R
   int32_t idx[18];
   int32_t z = 0;
   if constexpr (!LINKS_FIRST) z = prior_step_done();
-  if (i < n) load_links(adj, n, i, idx);
+  if (i < n) load_links(adj, ld, i, idx);
   if constexpr (LINKS_FIRST) z = prior_step_done();
   if (i < n) {
     C g[19];
     pull<PREC>(src, idx, i, k.inv_scale, g);
     collide<C, DAMPED>(g, k, DAMPED ? ld_nc(alpha + i) : C(0), rho, u);
 #pragma unroll
-    for (int q = 0; q < 19; ++q) store_stream<PREC>(dst + q * n + i, encode<PREC>(g[q], k.scale));
+    for (int q = 0; q < 19; ++q) store_stream<PREC>(dst + q * ld + i, encode<PREC>(g[q], k.scale));
   }
   if constexpr (RED != kNoReduce) {
     double w[4];
@@ -460,12 +463,13 @@ __device__ __forceinline__ uint32_t c_to_bits(float v, float scale) {
 // registers (4 blocks per SM).  The two accesses of a row are issued back to
 // back -- both cells' links, both pulls, and, after both collisions, both
 // stores -- so each pair lands on the same sectors at once and L1 and L2
-// merge them.  Loads stay scalar; a row whose element q N + i is even (every
-// row when N is even, the even rows otherwise) takes the pair's two stores
-// as one 4-byte store, which cuts the store instructions the LSU queue
-// holds.  FP16 on the 1024x256x256 bed, MFLUP/s, alternating runs: one cell
+// merge them.  Loads stay scalar; a row whose element q ld + i is even
+// (every row: the row stride ld is a multiple of kRowAlign) takes the pair's
+// two stores as one 4-byte store, which cuts the store instructions the LSU
+// queue holds.  FP16 on the 1024x256x256 bed, MFLUP/s, alternating runs: one cell
 // per thread 40,579-40,653; pair, all scalar 42,434-42,453; pair with the
-// 4-byte stores (this kernel) 43,307-43,376.  Measured slower in the same
+// 4-byte stores on the even rows of the odd list 43,307-43,376 (the rows of
+// stride N then; every row aligned: 45,537).  Measured slower in the same
 // runs: 4-byte stores on the other rows too, built with a lane shuffle,
 // 41,923; one 4-byte load for both pulls where they share a word 29,135;
 // 8-byte link loads on the aligned rows 29,844-30,936 (with and without the
@@ -496,12 +500,12 @@ __device__ __forceinline__ uint32_t ld_nc_u32(const uint32_t* p) {
 }
 
 // Pulls, both collisions and the stores of the pair (i, i + 1), given their
-// links a (cell i) and b (cell i + 1).
+// links a (cell i) and b (cell i + 1); dst rows of stride ld.
 template <int PREC, bool DAMPED>
 __device__ __forceinline__ void pair_body(const typename Form<PREC>::S* __restrict__ src,
-                                          typename Form<PREC>::S* __restrict__ dst, int32_t n,
+                                          typename Form<PREC>::S* __restrict__ dst, int32_t ld,
                                           const Coef<float>& k, const float* __restrict__ alpha,
-                                          int32_t i, bool two, bool odd_n, const int32_t a[18],
+                                          int32_t i, bool two, bool odd_ld, const int32_t a[18],
                                           const int32_t b[18]) {
   const unsigned short* src16 = reinterpret_cast<const unsigned short*>(src);
   // pulled values, packed: low half cell i, high half cell i + 1
@@ -536,8 +540,8 @@ __device__ __forceinline__ void pair_body(const typename Form<PREC>::S* __restri
   unsigned short* dst16 = reinterpret_cast<unsigned short*>(dst);
 #pragma unroll
   for (int q = 0; q < 19; ++q) {
-    const int32_t e = q * n + i;
-    if (two && !(odd_n && (q & 1))) {   // element e is even: one 4-byte store of the pair
+    const int32_t e = q * ld + i;
+    if (two && !(odd_ld && (q & 1))) {   // element e is even: one 4-byte store of the pair
       asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(dst16 + e), "r"(out[q]) : "memory");
     } else {
       st_cs(dst16 + e, (unsigned short)(out[q] & 0xffffu));
@@ -550,35 +554,36 @@ template <int PREC, bool DAMPED>
 __global__ void __launch_bounds__(kPairThreads, 4 * 256 / kPairThreads)
     sweep_pair_kernel(const typename Form<PREC>::S* __restrict__ src,
                       typename Form<PREC>::S* __restrict__ dst, const int32_t* __restrict__ adj,
-                      int32_t n, Coef<float> k, const float* __restrict__ alpha) {
+                      int32_t n, int32_t ld, Coef<float> k, const float* __restrict__ alpha) {
   static_assert(PREC == LBM_F16S || PREC == LBM_BF16S, "16-bit forms only");
   const int32_t z = prior_step_done();
   const int32_t i = 2 * (int32_t)(blockIdx.x * kPairThreads + threadIdx.x) + z;
   if (i >= n) return;
   const bool two = i + 1 < n;   // false only for the last cell of an odd-length list
-  const bool odd_n = (n & 1) != 0;
+  const bool odd_ld = (ld & 1) != 0;
   int32_t a[18], b[18];
 #pragma unroll
   for (int q = 0; q < 18; ++q) {
-    const int32_t* p = adj + q * n + i;
+    const int32_t* p = adj + q * ld + i;
     a[q] = ld_nc(p);
     b[q] = two ? ld_nc(p + 1) : 0;
   }
-  pair_body<PREC, DAMPED>(src, dst, n, k, alpha, i, two, odd_n, a, b);
+  pair_body<PREC, DAMPED>(src, dst, ld, k, alpha, i, two, odd_ld, a, b);
 }
 
-// Per-cell moments of the collision that a step from `src` performs.
+// Per-cell moments of the collision that a step from `src` performs (rows
+// of stride ld; rho_out [n], u_out [3][n]).
 template <int PREC, bool DAMPED>
 __global__ void __launch_bounds__(kSweepThreads)
     moments_kernel(const typename Form<PREC>::S* __restrict__ src, const int32_t* __restrict__ adj,
-                   int32_t n, Coef<typename Form<PREC>::C> k,
+                   int32_t n, int32_t ld, Coef<typename Form<PREC>::C> k,
                    const typename Form<PREC>::C* __restrict__ alpha, double* __restrict__ rho_out,
                    double* __restrict__ u_out) {
   using C = typename Form<PREC>::C;
   const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
   if (i >= n) return;
   C g[19];
-  gather<PREC>(src, adj, n, i, k.inv_scale, g);
+  gather<PREC>(src, adj, ld, i, k.inv_scale, g);
   C rho, u[3];
   collide<C, DAMPED>(g, k, DAMPED ? alpha[i] : C(0), rho, u);
   rho_out[i] = Form<PREC>::kShifted ? 1.0 + (double)rho : (double)rho;

@@ -47,10 +47,10 @@ struct RestRow {
 // One row q = blockIdx.y per grid row, so no slot index is divided by N.
 // From rest the stored value comes from `rest`; from f the value is
 // converted as the form stores it (the deviation f - w in FP64, then
-// rounded).
+// rounded).  f is [19][n]; dst has rows of stride ld.
 template <int PREC>
 __global__ void set_pdfs_kernel(typename Form<PREC>::S* __restrict__ dst,
-                                const double* __restrict__ f, int32_t n, double scale,
+                                const double* __restrict__ f, int32_t n, int32_t ld, double scale,
                                 RestRow<PREC> rest) {
   const int q = (int)blockIdx.y;
   using C = typename Form<PREC>::C;
@@ -60,28 +60,35 @@ __global__ void set_pdfs_kernel(typename Form<PREC>::S* __restrict__ dst,
   // block scheduling (2.9 ms for 1.25 GB)
   for (int32_t i = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); i < n;
        i += (int32_t)(gridDim.x * blockDim.x)) {
-    const int64_t t = (int64_t)q * n + i;
+    const int64_t t = (int64_t)q * ld + i;
     if (!f) {
       dst[t] = r;
     } else {
+      const double fv = f[(int64_t)q * n + i];
       C c;
-      if constexpr (Form<PREC>::kShifted) c = (C)(f[t] - w);
-      else c = (C)f[t];
+      if constexpr (Form<PREC>::kShifted) c = (C)(fv - w);
+      else c = (C)fv;
       dst[t] = encode<PREC>(c, (C)scale);
     }
   }
 }
 
+// The inverse of set_pdfs_kernel from f: src rows of stride ld, f [19][n].
 template <int PREC>
 __global__ void get_pdfs_kernel(const typename Form<PREC>::S* __restrict__ src, double* f,
-                                int32_t n, double inv_scale) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 19 * (int64_t)n) return;
-  const int q = (int)(t / n);
+                                int32_t n, int32_t ld, double inv_scale) {
+  const int q = (int)blockIdx.y;
   using C = typename Form<PREC>::C;
-  const double v = (double)decode<PREC>(src[t], (C)inv_scale);
-  f[t] = Form<PREC>::kShifted ? weight(q) + v : v;
+  const double w = weight(q);
+  for (int32_t i = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); i < n;
+       i += (int32_t)(gridDim.x * blockDim.x)) {
+    const double v = (double)decode<PREC>(src[(int64_t)q * ld + i], (C)inv_scale);
+    f[(int64_t)q * n + i] = Form<PREC>::kShifted ? w + v : v;
+  }
 }
+
+// Grid of the row kernels above: x blocks of 256 threads per row, 19 rows.
+dim3 row_grid(int64_t n) { return dim3((unsigned)std::min<int64_t>((n + 255) / 256, 2048), 19); }
 
 template <class C>
 __global__ void set_alpha_kernel(C* dst, const double* a, int32_t n) {
@@ -129,6 +136,7 @@ int launch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const dou
   using S = typename Form<PREC>::S;
   using C = typename Form<PREC>::C;
   const int32_t n = (int32_t)st->sp->n;
+  const int32_t ld = (int32_t)st->sp->ld;
   if constexpr (PREC == LBM_F64X) return launch_steps_fx(st, n_steps, wp, wm, F, stream, reduce_last);
   const Coef<C> k = make_coef<C>(wp, wm, F, st->scale_exp);
   const unsigned grid = (unsigned)st->nblocks;
@@ -143,7 +151,7 @@ int launch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const dou
     S* dst = (S*)st->buf[st->cur ^ 1];
     const bool last = reduce_last && t == n_steps - 1;
     if (n > 0) {
-      const int32_t* adj = st->sp->adj;
+      const int32_t* adj = state_links(st->sp);
       // Steps in FP64 arithmetic are not chained: a chained grid's blocks are
       // placed while the previous grid still holds its SMs, which packs
       // them onto fewer SMs, and these steps are bound by each SM's FP64
@@ -154,20 +162,20 @@ int launch_steps(lbm_state* st, int32_t n_steps, double wp, double wm, const dou
       const bool links_first = kMemoryBound && st->one_wave && !last;
       if constexpr (kPairForm) {
         if (!last && !st->one_wave) {
-          if (alpha) LBM_CUDA_TRY(launch_chained(sweep_pair_kernel<PREC, true>, grid_pair, (unsigned)kPairThreads, stream, chained, src, dst, adj, n, k, alpha));
-          else LBM_CUDA_TRY(launch_chained(sweep_pair_kernel<PREC, false>, grid_pair, (unsigned)kPairThreads, stream, chained, src, dst, adj, n, k, alpha));
+          if (alpha) LBM_CUDA_TRY(launch_chained(sweep_pair_kernel<PREC, true>, grid_pair, (unsigned)kPairThreads, stream, chained, src, dst, adj, n, ld, k, alpha));
+          else LBM_CUDA_TRY(launch_chained(sweep_pair_kernel<PREC, false>, grid_pair, (unsigned)kPairThreads, stream, chained, src, dst, adj, n, ld, k, alpha));
           st->cur ^= 1;
           continue;
         }
       }
       if (alpha) {
-        if (last) LBM_CUDA_TRY(launch_sweep(sweep_kernel<PREC, true, kWarpSums>, grid, stream, chained, src, dst, adj, n, k, alpha, st->partials));
-        else if (links_first) LBM_CUDA_TRY(launch_sweep(sweep_kernel<PREC, true, kNoReduce, kMemoryBound>, grid, stream, chained, src, dst, adj, n, k, alpha, st->partials));
-        else LBM_CUDA_TRY(launch_sweep(sweep_kernel<PREC, true, kNoReduce>, grid, stream, chained, src, dst, adj, n, k, alpha, st->partials));
+        if (last) LBM_CUDA_TRY(launch_sweep(sweep_kernel<PREC, true, kWarpSums>, grid, stream, chained, src, dst, adj, n, ld, k, alpha, st->partials));
+        else if (links_first) LBM_CUDA_TRY(launch_sweep(sweep_kernel<PREC, true, kNoReduce, kMemoryBound>, grid, stream, chained, src, dst, adj, n, ld, k, alpha, st->partials));
+        else LBM_CUDA_TRY(launch_sweep(sweep_kernel<PREC, true, kNoReduce>, grid, stream, chained, src, dst, adj, n, ld, k, alpha, st->partials));
       } else {
-        if (last) LBM_CUDA_TRY(launch_sweep(sweep_kernel<PREC, false, kWarpSums>, grid, stream, chained, src, dst, adj, n, k, alpha, st->partials));
-        else if (links_first) LBM_CUDA_TRY(launch_sweep(sweep_kernel<PREC, false, kNoReduce, kMemoryBound>, grid, stream, chained, src, dst, adj, n, k, alpha, st->partials));
-        else LBM_CUDA_TRY(launch_sweep(sweep_kernel<PREC, false, kNoReduce>, grid, stream, chained, src, dst, adj, n, k, alpha, st->partials));
+        if (last) LBM_CUDA_TRY(launch_sweep(sweep_kernel<PREC, false, kWarpSums>, grid, stream, chained, src, dst, adj, n, ld, k, alpha, st->partials));
+        else if (links_first) LBM_CUDA_TRY(launch_sweep(sweep_kernel<PREC, false, kNoReduce, kMemoryBound>, grid, stream, chained, src, dst, adj, n, ld, k, alpha, st->partials));
+        else LBM_CUDA_TRY(launch_sweep(sweep_kernel<PREC, false, kNoReduce>, grid, stream, chained, src, dst, adj, n, ld, k, alpha, st->partials));
       }
     }
     st->cur ^= 1;
@@ -185,9 +193,9 @@ int launch_moments(const lbm_state* st, double* rho, double* u) {
   const S* prev = (const S*)st->buf[st->cur ^ 1];
   const C* alpha = (const C*)st->alpha;
   if (alpha)
-    moments_kernel<PREC, true><<<(unsigned)st->nblocks, kSweepThreads, 0, st->sp->stream>>>(prev, st->sp->adj, n, k, alpha, rho, u);
+    moments_kernel<PREC, true><<<(unsigned)st->nblocks, kSweepThreads, 0, st->sp->stream>>>(prev, state_links(st->sp), n, (int32_t)st->sp->ld, k, alpha, rho, u);
   else
-    moments_kernel<PREC, false><<<(unsigned)st->nblocks, kSweepThreads, 0, st->sp->stream>>>(prev, st->sp->adj, n, k, alpha, rho, u);
+    moments_kernel<PREC, false><<<(unsigned)st->nblocks, kSweepThreads, 0, st->sp->stream>>>(prev, state_links(st->sp), n, (int32_t)st->sp->ld, k, alpha, rho, u);
   LBM_CUDA_TRY(cudaGetLastError());
   return LBM_OK;
 }
@@ -212,10 +220,9 @@ int launch_set(lbm_state* st, const double* f, int from_rest) {
     }
   }
   const int32_t n = (int32_t)st->sp->n;
-  const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 2048);
-  set_pdfs_kernel<PREC><<<dim3(blocks, 19), 256, 0, st->sp->stream>>>(
+  set_pdfs_kernel<PREC><<<row_grid(n), 256, 0, st->sp->stream>>>(
       (S*)st->buf[grouped ? st->cur ^ 1 : st->cur], from_rest ? nullptr : f, n,
-      std::ldexp(1.0, st->scale_exp), rest);
+      (int32_t)st->sp->ld, std::ldexp(1.0, st->scale_exp), rest);
   LBM_CUDA_TRY(cudaGetLastError());
   if (grouped) return batch_relayout_pdfs(st, st->cur ^ 1, st->cur, false);
   return LBM_OK;
@@ -230,9 +237,9 @@ int launch_get(const lbm_state* st, double* f) {
     const int rc = batch_relayout_pdfs(st, st->cur, st->cur ^ 1, true);
     if (rc != LBM_OK) return rc;
   }
-  get_pdfs_kernel<PREC><<<(unsigned)((total + 255) / 256), 256, 0, st->sp->stream>>>(
+  get_pdfs_kernel<PREC><<<row_grid(st->sp->n), 256, 0, st->sp->stream>>>(
       (const typename Form<PREC>::S*)st->buf[grouped ? st->cur ^ 1 : st->cur], f,
-      (int32_t)st->sp->n, std::ldexp(1.0, -st->scale_exp));
+      (int32_t)st->sp->n, (int32_t)st->sp->ld, std::ldexp(1.0, -st->scale_exp));
   LBM_CUDA_TRY(cudaGetLastError());
   return LBM_OK;
 }
@@ -371,6 +378,8 @@ extern "C" int lbm_state_create(const lbm_sparse* sp, int32_t precision, int32_t
   if (!out) return fail(LBM_EINVAL, "out is NULL");
   *out = nullptr;
   if (!sp || sp->magic != kMagicSparse) return fail(LBM_EINVAL, "not a sparse handle");
+  if (sp->ld < sp->n || (sp->ld != sp->n && !sp->adj_ld))
+    return fail(LBM_EINVAL, "sparse handle without a valid row layout");
   if (precision < LBM_F64 || precision > LBM_F64X)
     return fail(LBM_EINVAL, "unknown precision %d", precision);
   if ((precision == LBM_F16S || precision == LBM_BF16S) && (scale_exp < 0 || scale_exp > 40))
@@ -392,7 +401,8 @@ extern "C" int lbm_state_create(const lbm_sparse* sp, int32_t precision, int32_t
   }
   // one wave at the 4 resident blocks per SM of the FP32 and 16-bit sweeps
   st->one_wave = st->nblocks <= 4 * (int64_t)sms;
-  const size_t bytes = storage_bytes(precision) * 19 * (size_t)(n > 0 ? n : 1);
+  // rows of sp->ld elements; the padding slots past n are never read
+  const size_t bytes = storage_bytes(precision) * 19 * (size_t)(sp->ld > 0 ? sp->ld : 1);
   const cudaStream_t stream = sp->stream;
   bool ok = dev_alloc(&st->buf[0], bytes, stream, false) == cudaSuccess &&
             dev_alloc(&st->buf[1], bytes, stream, false) == cudaSuccess &&
@@ -668,10 +678,10 @@ extern "C" int lbm_step_f64_noalloc(const double* f_src_dev, double* f_dst_dev,
   const Coef<double> k = make_coef<double>(omega_plus, omega_minus, force, 0);
   if (alpha_dev)
     sweep_kernel<LBM_F64, true, kBlockSums><<<(unsigned)nblocks, kSweepThreads, 0, stream>>>(
-        f_src_dev, f_dst_dev, adj_dev, n, k, alpha_dev, partials);
+        f_src_dev, f_dst_dev, adj_dev, n, n, k, alpha_dev, partials);
   else
     sweep_kernel<LBM_F64, false, kBlockSums><<<(unsigned)nblocks, kSweepThreads, 0, stream>>>(
-        f_src_dev, f_dst_dev, adj_dev, n, k, nullptr, partials);
+        f_src_dev, f_dst_dev, adj_dev, n, n, k, nullptr, partials);
   final_sum_kernel<<<1, 1024, 0, stream>>>(partials, nblocks, sums_dev);
   LBM_CUDA_TRY(cudaGetLastError());
   return LBM_OK;

@@ -161,7 +161,7 @@ template <bool HP_POW2>
 __device__ __forceinline__ void fx_collide_store(const int64_t S[9], const int64_t D[9],
                                                  int64_t drho, int64_t ux, int64_t uy,
                                                  int64_t uz, const FxCoef& k, int64_t a1,
-                                                 double* __restrict__ dst, int32_t n, int32_t i) {
+                                                 double* __restrict__ dst, int32_t ld, int32_t i) {
   // a1: the odd-part coefficient w-/6 (undamped) or w-/6 - b1 alpha, * 2^63
   const int64_t V1x = fxmul(ux, a1) + k.bF1[0];
   const int64_t V1y = fxmul(uy, a1) + k.bF1[1];
@@ -223,12 +223,12 @@ __device__ __forceinline__ void fx_collide_store(const int64_t S[9], const int64
   for (int q = 0; q < 19; ++q) {
     const int64_t bits = wbits(q) + d[q];
     out_of_range |= (uint32_t)((bits >> 52) != wexp(q)) << q;
-    st_cs(dst + q * n + i, __longlong_as_double(bits));
+    st_cs(dst + q * ld + i, __longlong_as_double(bits));
   }
   if (out_of_range) {
     for (int q = 0; q < 19; ++q)
       if ((out_of_range >> q) & 1u)
-        dst[q * n + i] = weight(q) + (double)(d[q] << wshift(q)) * 0x1p-58;
+        dst[q * ld + i] = weight(q) + (double)(d[q] << wshift(q)) * 0x1p-58;
   }
 }
 
@@ -236,11 +236,11 @@ __device__ __forceinline__ void fx_collide_store(const int64_t S[9], const int64
 template <bool DAMPED>
 __device__ __forceinline__ void fx_ieee_collide_store(double g[19], const Coef<double>& kd,
                                                       double alpha, double* __restrict__ dst,
-                                                      int32_t n, int32_t i, double red[4]) {
+                                                      int32_t ld, int32_t i, double red[4]) {
   double rho, u[3];
   collide<double, DAMPED>(g, kd, alpha, rho, u);
 #pragma unroll
-  for (int q = 0; q < 19; ++q) st_cs(dst + q * n + i, g[q]);
+  for (int q = 0; q < 19; ++q) st_cs(dst + q * ld + i, g[q]);
   red[0] = rho;
   red[1] = u[0];
   red[2] = u[1];
@@ -267,28 +267,29 @@ __device__ __forceinline__ bool fx_damp(const int64_t* __restrict__ alpha_fx, in
   return true;
 }
 
-// A step that does not reduce.
+// A step that does not reduce: n cells, PDF and link rows of stride ld.
 template <bool HP_POW2, bool DAMPED>
 __global__ void __launch_bounds__(kSweepThreads, LBM_FX_MIN_BLOCKS)
     sweep_fx_kernel(const double* __restrict__ src, double* __restrict__ dst,
-                    const int32_t* __restrict__ adj, int32_t n, FxCoef k, Coef<double> kd,
-                    const double* __restrict__ alpha, const int64_t* __restrict__ alpha_fx) {
+                    const int32_t* __restrict__ adj, int32_t n, int32_t ld, FxCoef k,
+                    Coef<double> kd, const double* __restrict__ alpha,
+                    const int64_t* __restrict__ alpha_fx) {
   const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
   prior_step_done();  // a chained launch waits here for the previous step
   if (i < n) {
     int32_t idx[18];
     int64_t b[19];
-    load_links(adj, n, i, idx);
+    load_links(adj, ld, i, idx);
     fx_pull(src, idx, i, b);
     int64_t S[9], D[9], drho = 0, ux = 0, uy = 0, uz = 0, a1 = 0;
     if (fx_moments(b, k, S, D, drho, ux, uy, uz) &&
         fx_damp<DAMPED>(alpha_fx, n, i, k, ux, uy, uz, a1)) {
-      fx_collide_store<HP_POW2>(S, D, drho, ux, uy, uz, k, a1, dst, n, i);
+      fx_collide_store<HP_POW2>(S, D, drho, ux, uy, uz, k, a1, dst, ld, i);
     } else {
       double g[19], red[4];
 #pragma unroll
       for (int q = 0; q < 19; ++q) g[q] = __longlong_as_double(b[q]);
-      fx_ieee_collide_store<DAMPED>(g, kd, DAMPED ? ld_nc(alpha + i) : 0.0, dst, n, i, red);
+      fx_ieee_collide_store<DAMPED>(g, kd, DAMPED ? ld_nc(alpha + i) : 0.0, dst, ld, i, red);
     }
   }
 }
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_FX_MIN_BLOCKS)
 template <bool HP_POW2, bool DAMPED>
 __global__ void __launch_bounds__(kSweepThreads, LBM_FX_RED_MIN_BLOCKS)
     sweep_fx_reduce_kernel(const double* __restrict__ src, double* __restrict__ dst,
-                           const int32_t* __restrict__ adj, int32_t n, FxCoef k,
+                           const int32_t* __restrict__ adj, int32_t n, int32_t ld, FxCoef k,
                            Coef<double> kd, const double* __restrict__ alpha,
                            const int64_t* __restrict__ alpha_fx, double* __restrict__ partials) {
   const int32_t i = blockIdx.x * kSweepThreads + threadIdx.x;
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_FX_RED_MIN_BLOCKS)
   if (live) {
     int32_t idx[18];
     int64_t b[19];
-    load_links(adj, n, i, idx);
+    load_links(adj, ld, i, idx);
     fx_pull(src, idx, i, b);
     fast = fx_moments(b, k, S, D, drho, ux, uy, uz) &&
            fx_damp<DAMPED>(alpha_fx, n, i, k, ux, uy, uz, a1);
@@ -322,13 +323,13 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_FX_RED_MIN_BLOCKS)
   double red[4] = {0.0, 0.0, 0.0, 0.0};   // IEEE-path cells: rho, u
   if (live) {
     if (fast) {
-      fx_collide_store<HP_POW2>(S, D, drho, ux, uy, uz, k, a1, dst, n, i);
+      fx_collide_store<HP_POW2>(S, D, drho, ux, uy, uz, k, a1, dst, ld, i);
     } else {
       double g[19];
       g[0] = ld_nc(src + i);
 #pragma unroll
-      for (int q = 1; q < 19; ++q) g[q] = ld_nc(src + __ldg(adj + (q - 1) * n + i));
-      fx_ieee_collide_store<DAMPED>(g, kd, DAMPED ? ld_nc(alpha + i) : 0.0, dst, n, i, red);
+      for (int q = 1; q < 19; ++q) g[q] = ld_nc(src + __ldg(adj + (q - 1) * ld + i));
+      fx_ieee_collide_store<DAMPED>(g, kd, DAMPED ? ld_nc(alpha + i) : 0.0, dst, ld, i, red);
     }
   }
   fx_ieee_warp_add(red, live && !fast, partials + z);
@@ -365,19 +366,19 @@ FxCoef make_fx_coef(double wp, double wm, const double F[3], bool* pow2) {
   return k;
 }
 
-// One fixed-point step of state st from src to dst (its damping included);
-// partials non-null: the reducing variant.
-cudaError_t launch_fx(const lbm_state* st, const double* src, double* dst, const FxCoef& k,
-                      bool pow2, const Coef<double>& kd, cudaStream_t stream, bool chained,
-                      double* partials) {
+// One fixed-point step of state st (its damping included) from src to dst,
+// arrays of rows of stride ld read through links adj; partials non-null: the
+// reducing variant.
+cudaError_t launch_fx(const lbm_state* st, const double* src, double* dst, const int32_t* adj,
+                      int32_t ld, const FxCoef& k, bool pow2, const Coef<double>& kd,
+                      cudaStream_t stream, bool chained, double* partials) {
   const int32_t n = (int32_t)st->sp->n;
   const unsigned grid = (unsigned)st->nblocks;
-  const int32_t* adj = st->sp->adj;
   const double* alpha = (const double*)st->alpha;
   const int64_t* afx = st->alpha_fx;
 #define LBM_FX_LAUNCH(P2, DA)                                                                       \
-  return partials ? launch_sweep(sweep_fx_reduce_kernel<P2, DA>, grid, stream, chained, src, dst, adj, n, k, kd, alpha, afx, partials) \
-                  : launch_sweep(sweep_fx_kernel<P2, DA>, grid, stream, chained, src, dst, adj, n, k, kd, alpha, afx)
+  return partials ? launch_sweep(sweep_fx_reduce_kernel<P2, DA>, grid, stream, chained, src, dst, adj, n, ld, k, kd, alpha, afx, partials) \
+                  : launch_sweep(sweep_fx_kernel<P2, DA>, grid, stream, chained, src, dst, adj, n, ld, k, kd, alpha, afx)
   if (alpha) {
     if (pow2) LBM_FX_LAUNCH(true, true);
     LBM_FX_LAUNCH(false, true);
@@ -399,20 +400,22 @@ int launch_steps_fx(lbm_state* st, int32_t n_steps, double wp, double wm, const 
     double* dst = (double*)st->buf[st->cur ^ 1];
     if (st->sp->n > 0) {
       const bool last = reduce_last && t == n_steps - 1;
-      LBM_CUDA_TRY(launch_fx(st, src, dst, k, pow2, kd, stream, t > 0, last ? st->partials : nullptr));
+      LBM_CUDA_TRY(launch_fx(st, src, dst, state_links(st->sp), (int32_t)st->sp->ld, k, pow2, kd,
+                             stream, t > 0, last ? st->partials : nullptr));
     }
     st->cur ^= 1;
   }
   return LBM_OK;
 }
 
-int launch_fx_step(const lbm_state* st, const double* src, double* dst, double wp, double wm,
-                   const double F[3], cudaStream_t stream, bool chained) {
+int launch_fx_step(const lbm_state* st, const double* src, double* dst, const int32_t* adj,
+                   int32_t ld, double wp, double wm, const double F[3], cudaStream_t stream,
+                   bool chained) {
   if (st->sp->n == 0) return LBM_OK;
   bool pow2 = false;
   const FxCoef k = make_fx_coef(wp, wm, F, &pow2);
   const Coef<double> kd = make_coef<double>(wp, wm, F, 0);
-  LBM_CUDA_TRY(launch_fx(st, src, dst, k, pow2, kd, stream, chained, nullptr));
+  LBM_CUDA_TRY(launch_fx(st, src, dst, adj, ld, k, pow2, kd, stream, chained, nullptr));
   return LBM_OK;
 }
 

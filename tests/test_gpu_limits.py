@@ -1,14 +1,17 @@
 """The index-range limits of the int32 adjacency, at full size.
 
-A flow slot is addressed as q*N + m in int32, so the library accepts at most
-19*N < 2^31 fluid cells (N <= 113,025,455).  An all-fluid periodic box just
-below that limit (1024 x 512 x 215 = 112,721,920 cells, the last PDF slot
-at 2,141,716,479) is assembled and stepped in the FP64-storage form: every
-cell sees the same history, so every cell's moments must equal those of a
-single periodic cell stepped by the oracle, and the mass must stay N.  Any
-index that wrapped past 2^31 would break that uniformity.  A slightly
-larger all-fluid box (1024 x 512 x 256, 19*N = 2.55e9) must be refused with
-LBM_EOVERFLOW before any PDF or adjacency memory is taken.
+A state's PDF slot is addressed as q*L + m in int32, L the row stride (N
+rounded up to 64), so the library accepts at most 19*L < 2^31 (N <=
+113,025,408).  All-fluid periodic boxes just below that limit are assembled
+and stepped in the FP64-storage form: 1024 x 512 x 215 = 112,721,920 cells
+(L = N, the last PDF slot at 2,141,716,479) and 1023 x 511 x 215 =
+112,391,895 cells (rows padded to L = 112,391,936, the last slot at
+2,135,446,783).  Every cell sees the same history, so every cell's moments
+must equal those of a single periodic cell stepped by the oracle, and the
+mass must stay N.  Any index that wrapped past 2^31 would break that
+uniformity.  A slightly larger all-fluid box (1024 x 512 x 256, 19*N =
+2.55e9) must be refused with LBM_EOVERFLOW before any PDF or adjacency
+memory is taken.
 """
 import numpy as np
 import pytest
@@ -30,10 +33,12 @@ def library():
     capi.load()
 
 
-def test_largest_list_steps_uniformly():
-    dims = (1024, 512, 215)          # x, y, z
+@pytest.mark.parametrize("dims", [(1024, 512, 215), (1023, 511, 215)])   # x, y, z
+def test_largest_list_steps_uniformly(dims):
     n_box = dims[0] * dims[1] * dims[2]
-    assert 19 * n_box < 2 ** 31 <= 19 * 1024 * 512 * 216
+    ld = -(-n_box // 64) * 64
+    assert 19 * ld < 2 ** 31 <= 19 * 1024 * 512 * 216
+    assert (ld == n_box) == (dims[0] == 1024)
     flags = torch.zeros((dims[2], dims[1], dims[0]), dtype=torch.uint8, device="cuda")
     lat = SparseLattice(flags, "lex", periodic=0b111)
     del flags
@@ -66,4 +71,4 @@ def test_list_beyond_the_slot_range_is_refused():
     with pytest.raises(capi.LbmError) as ei:
         SparseLattice(flags, "lex", periodic=0b111)
     assert ei.value.status == capi.LBM_EOVERFLOW
-    assert "19*N" in str(ei.value)
+    assert "19*L" in str(ei.value)

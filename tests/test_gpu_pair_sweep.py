@@ -4,7 +4,8 @@ Its plain steps run on grids of more than one wave, and the reducing last
 step of a call runs the one-cell kernel, so a run taken in one call must
 equal the same steps taken one call each bit for bit (same per-cell
 arithmetic).  The cases cover both parities of the list length N (an odd
-N leaves one cell alone at the end of the list),
+N leaves one cell alone at the end of the list) and an N that needs no
+row padding,
 damping, and an order in which neighbouring cells rarely pull from
 neighbouring slots (Morton, 2-bit) as well as the lexicographic order in
 which they mostly do.
@@ -22,17 +23,29 @@ WM = omega_minus(WP)
 F = (2e-6, -1e-6, 1e-5)
 
 
-@pytest.fixture(scope="module", params=["even", "odd"])
+@pytest.fixture(scope="module", params=["even", "odd", "x64"])
 def flags(request):
+    """N even, N odd (rows padded to a multiple of 64 either way), and N a
+    multiple of 64 (rows unpadded; the kernels read the plain links)."""
     build.build()
     capi.load()
     bed = inputs.packed_bed((96, 80, 72), 2, 70.0, 5.0, 0.45, 3)
     f = bed.flags.copy()
-    want = 0 if request.param == "even" else 1
-    if int((f == 0).sum()) % 2 != want:
-        z, y, x = np.argwhere(f == 0)[len(np.argwhere(f == 0)) // 2]
+    fluid = np.argwhere(f == 0)
+    mid = len(fluid) // 2
+    if request.param == "x64":
+        drop = len(fluid) % 64
+    else:
+        want = 0 if request.param == "even" else 1
+        drop = 0 if len(fluid) % 2 == want else 1
+        if (len(fluid) - drop) % 64 == 0:
+            drop += 2
+    for z, y, x in fluid[mid:mid + drop]:
         f[z, y, x] = 1
-    assert int((f == 0).sum()) % 2 == want
+    n = int((f == 0).sum())
+    assert (n % 64 == 0) == (request.param == "x64")
+    if request.param != "x64":
+        assert n % 2 == (0 if request.param == "even" else 1)
     return f, bed.periodic
 
 

@@ -37,13 +37,23 @@ F = (3e-6, -2e-6, 5e-6)
 DEV = 1e-4
 
 
-@pytest.fixture(scope="module")
-def lattice():
+@pytest.fixture(scope="module", params=["ragged", "x64"])
+def lattice(request):
+    """The small bed (a list whose length is not a multiple of the 64-element
+    row alignment, so the state's rows are padded) and the same bed with
+    its last fluid cells made solid until the length is one (rows unpadded)."""
     build.build()
     capi.load()
     bed = inputs.bed_small(1)
-    cells, _, adj = oracle.build_sparse(bed.flags, oracle.ORDER_LEX, periodic=bed.periodic)
-    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "lex", periodic=bed.periodic)
+    flags = bed.flags.copy()
+    fluid = np.argwhere(flags == 0)
+    assert len(fluid) % 64 != 0
+    if request.param == "x64":
+        for z, y, x in fluid[len(fluid) - len(fluid) % 64:]:
+            flags[z, y, x] = 1
+    cells, _, adj = oracle.build_sparse(flags, oracle.ORDER_LEX, periodic=bed.periodic)
+    assert (len(cells) % 64 == 0) == (request.param == "x64")
+    lat = SparseLattice(torch.from_numpy(flags).cuda(), "lex", periodic=bed.periodic)
     np.testing.assert_array_equal(lat.cells().cpu().numpy(), cells)
     yield lat, adj, len(cells)
     lat.close()

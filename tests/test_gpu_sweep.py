@@ -80,6 +80,34 @@ def test_tiny_boxes_random_state_parity(shape, periodic, precision):
         lat.close()
 
 
+@pytest.mark.parametrize("precision", ["f64", "f64x"])
+@pytest.mark.parametrize("shape", [(4, 4, 4), (4, 4, 8), (3, 43, 1), (1, 1, 65)])
+def test_row_alignment_edges_parity(shape, precision):
+    """Fully fluid periodic boxes of 64 and 128 cells (state rows of exactly
+    N elements, read through the plain links) and of 129 and 65 cells (rows
+    padded to 192 and 128 elements, read through the padded links): random
+    state, damping and force against the oracle."""
+    rng = np.random.default_rng(sum(shape))
+    flags = np.zeros(shape, np.uint8)
+    f0 = oracle.rest_state(flags) * (1 + 0.05 * rng.standard_normal((19,) + shape))
+    alpha = 0.05 * rng.random(shape)
+    F = 1e-3 * rng.standard_normal(3)
+    for steps in (1, 4):
+        lat, st, cells = _gpu_run(flags, 7, steps, F, precision=precision, alpha_dense=alpha,
+                                  f0_dense=f0)
+        assert lat.n == flags.size
+        f_ref, obs, _, u_ref = oracle.run(flags, 7, WP, WM, F, steps, alpha=alpha, f=f0)
+        rho, u = st.moments()
+        fp64_measures.check(st.get_pdfs().cpu().numpy(), oracle.to_sparse(f_ref, cells), steps,
+                            u.cpu().numpy(), oracle.to_sparse(u_ref, cells),
+                            label=f"box {shape} {precision}")
+        mass, flux = st.reduce_flux(0)
+        assert abs(mass - obs[-1, 0]) < 1e-13 * abs(obs[-1, 0])
+        assert abs(flux - obs[-1, 1] / lat.n) < 1e-13 * max(np.abs(u_ref).max(), 1e-30)
+        st.close()
+        lat.close()
+
+
 @pytest.mark.parametrize("precision", ["f64", "f32s"])
 def test_reduction_of_large_moments_takes_the_fp64_path(precision):
     """States far from rest (|rho - 1| and |u| up to ~1): warps holding a
