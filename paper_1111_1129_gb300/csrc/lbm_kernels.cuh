@@ -466,12 +466,12 @@ __device__ __forceinline__ uint32_t c_to_bits(float v, float scale) {
 // merge them.  Loads stay scalar; a row whose element q ld + i is even
 // (every row: the row stride ld is a multiple of kRowAlign) takes the pair's
 // two stores as one 4-byte store, which cuts the store instructions the LSU
-// queue holds.  FP16 on the 1024x256x256 bed, MFLUP/s, alternating runs: one cell
-// per thread 40,579-40,653; pair, all scalar 42,434-42,453; pair with the
-// 4-byte stores on the even rows of the odd list 43,307-43,376 (the rows of
-// stride N then; every row aligned: 45,537).  Measured slower in the same
-// runs: 4-byte stores on the other rows too, built with a lane shuffle,
-// 41,923; one 4-byte load for both pulls where they share a word 29,135;
+// queue holds.  FP16 on the 1024x256x256 bed (N odd), MFLUP/s: with rows of
+// stride N, alternating runs: one cell per thread 40,579-40,653; pair, all
+// scalar 42,434-42,453; pair with the 4-byte stores on the even rows
+// 43,307-43,376.  With every row aligned (this kernel) 45,779-45,784.
+// Measured slower, on rows of stride N: 4-byte stores on the odd rows too,
+// built with a lane shuffle, 41,923; one 4-byte load for both pulls where they share a word 29,135;
 // 8-byte link loads on the aligned rows 29,844-30,936 (with and without the
 // L2 hint, non-coherent or coherent; with registers to spare, 78 at 3 blocks
 // per SM, 25,215 against 41,622 for scalar loads at that occupancy, so not
