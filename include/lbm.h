@@ -129,11 +129,14 @@ int lbm_ordering_keys(const int32_t dims[3], lbm_ordering ord, uint64_t* keys_de
  * out:       receives a library-owned handle holding, in device memory,
  *            cells[N] (box index of the fluid cell with I_c = n + 1, i.e.
  *            fluid cells ranked by key), inv[nx*ny*nz] (n, or -1 for solid)
- *            and adj[18*N] (layout above).  Unless N is a multiple of 64 it
- *            also holds the same links in the layout the states keep
- *            internally (rows of L = N rounded up to 64 slots, so that
- *            every row starts on a 128-byte boundary; 72 bytes per L), which
- *            the steps read; lbm_sparse_info presents adj only.
+ *            and the adjacency.  The states keep their arrays in rows of
+ *            L slots, L = N rounded up to 64, so that every row starts on a
+ *            128-byte boundary; the adjacency is stored in that layout
+ *            (18 rows of L, entries r*L + m; 72 bytes per L), which the
+ *            steps read.  When L = N that is adj[18*N] of the layout above;
+ *            otherwise adj[18*N] is derived from it on its first request
+ *            (lbm_sparse_info, lbm_adjoint_create, lbm_state_create_batched)
+ *            and then kept.
  * The call synchronises `stream` (to learn N, and again before returning,
  * so the flags may be released afterwards).  Errors: LBM_EINVAL,
  * LBM_EFLAGS, LBM_EOVERFLOW (19*L >= 2^31), LBM_ENOMEM, LBM_ECUDA.
@@ -143,7 +146,10 @@ int lbm_build_sparse(const uint8_t* flags, const int32_t dims[3], lbm_ordering o
 
 /*
  * Read-only views of a sparse representation.  Any out pointer may be NULL.
- * The device pointers stay owned by the handle.
+ * The device pointers stay owned by the handle.  adj_dev is adj[18*N] of the
+ * layout above; when N is not a multiple of 64 the first request builds it
+ * (72 bytes per cell of device memory, one kernel on the handle's stream,
+ * which the call then synchronises) and may fail with LBM_ENOMEM.
  */
 int lbm_sparse_info(const lbm_sparse* sp, int64_t* n_fluid, const int32_t** cells_dev,
                     const int32_t** adj_dev, const int32_t** inv_dev);

@@ -779,6 +779,9 @@ extern "C" int lbm_adjoint_create(const lbm_state* st, int32_t n_steps, int32_t 
   if (stride < 0) return fail(LBM_EINVAL, "checkpoint stride %d < 0", stride);
   if (stride == 0) stride = (int32_t)std::ceil(std::sqrt((double)n_steps));
   if (stride > n_steps) stride = n_steps;
+  // the adjoint's arrays are [19][N], read through the public links
+  const int rc = public_links(st->sp, nullptr);
+  if (rc != LBM_OK) return rc;
   lbm_adjoint* ad = new lbm_adjoint{};
   ad->magic = kMagicAdjoint;
   ad->st = st;

@@ -124,13 +124,12 @@ __global__ void __launch_bounds__(kTileThreads)
   }
 }
 
-// Pull adjacency (Sec. 2): source slot of direction i for fluid cell n.
-// adj_ld (or null): the same links in the state layout, rows of ld entries
-// naming slot r ld + m.
+// Pull adjacency (Sec. 2): source slot of direction i for fluid cell n, in
+// rows of ld >= n entries naming slot r ld + m (ld = n: the public layout).
 __global__ void adjacency_kernel(int32_t nx, int32_t ny, int32_t nz, uint32_t periodic,
                                  const int32_t* __restrict__ cells,
                                  const int32_t* __restrict__ inv, int32_t* __restrict__ adj,
-                                 int32_t n, int32_t* __restrict__ adj_ld, int32_t ld) {
+                                 int32_t n, int32_t ld) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int32_t c = cells[i];
@@ -150,9 +149,20 @@ __global__ void adjacency_kernel(int32_t nx, int32_t ny, int32_t nz, uint32_t pe
     }
     int32_t m = -1;
     if (inside) m = inv[sx + nx * (sy + ny * sz)];
-    adj[(q - 1) * n + i] = m >= 0 ? q * n + m : opp(q) * n + i;
-    if (adj_ld) adj_ld[(q - 1) * ld + i] = m >= 0 ? q * ld + m : opp(q) * ld + i;
+    adj[(q - 1) * ld + i] = m >= 0 ? q * ld + m : opp(q) * ld + i;
   }
+}
+
+// The public links (rows of n, slot q n + m) from links in rows of ld > n
+// (slot r ld + m); grid (cells, 18 rows).
+__global__ void public_links_kernel(const int32_t* __restrict__ adj_ld, int32_t ld, int32_t n,
+                                    int32_t* __restrict__ adj) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int32_t q = (int32_t)blockIdx.y;
+  if (i >= n) return;
+  const uint32_t s = (uint32_t)adj_ld[q * ld + i];
+  const uint32_t r = s / (uint32_t)ld;
+  adj[q * n + i] = (int32_t)(r * (uint32_t)n + (s - r * (uint32_t)ld));
 }
 
 }  // namespace
@@ -210,6 +220,34 @@ int make_key_space(const int32_t dims[3], const lbm_ordering& ord, bool clamp_bl
     s.size = key_of(s, s.nx - 1, s.ny - 1, s.nz - 1) + 1;
   }
   *ks = s;
+  return LBM_OK;
+}
+
+int public_links(const lbm_sparse* sp_c, const int32_t** out) {
+  // logically const: the public links are a cached view of adj_ld
+  lbm_sparse* sp = const_cast<lbm_sparse*>(sp_c);
+  if (!sp->adj) {
+    const cudaStream_t stream = sp->stream;
+    int32_t* adj = nullptr;
+    if (dev_alloc(&adj, sizeof(int32_t) * 18 * (size_t)(sp->n > 0 ? sp->n : 1), stream, true) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return fail(LBM_ENOMEM, "public adjacency allocation failed (%lld fluid cells)",
+                  (long long)sp->n);
+    }
+    if (sp->n > 0)
+      public_links_kernel<<<dim3((unsigned)((sp->n + 255) / 256), 18), 256, 0, stream>>>(
+          sp->adj_ld, (int32_t)sp->ld, (int32_t)sp->n, adj);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+      dev_free(adj, stream, true);
+      cudaStreamSynchronize(stream);
+      return cuda_fail(e, "public adjacency");
+    }
+    sp->adj = adj;
+  }
+  if (out) *out = sp->adj;
   return LBM_OK;
 }
 
@@ -317,9 +355,10 @@ extern "C" int lbm_build_sparse(const uint8_t* flags, const int32_t dims[3], lbm
   sp->n = n;
   sp->ld = ld;
   const size_t nn = (size_t)(n > 0 ? n : 1);
+  // the links in the state layout; they are the public ones when ld == n
+  int32_t** links = ld == n ? &sp->adj : &sp->adj_ld;
   if (dev_alloc(&sp->cells, sizeof(int32_t) * nn, stream, true) != cudaSuccess ||
-      dev_alloc(&sp->adj, sizeof(int32_t) * 18 * nn, stream, true) != cudaSuccess ||
-      (ld != n && dev_alloc(&sp->adj_ld, sizeof(int32_t) * 18 * (size_t)ld, stream, true) != cudaSuccess)) {
+      dev_alloc(links, sizeof(int32_t) * 18 * (size_t)(ld > 0 ? ld : 1), stream, true) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(LBM_ENOMEM, "device allocation failed (%lld fluid cells)", (long long)n));
   }
@@ -328,8 +367,8 @@ extern "C" int lbm_build_sparse(const uint8_t* flags, const int32_t dims[3], lbm
   if (n > 0) {
     const int threads = 256;
     adjacency_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, stream>>>(
-        dims[0], dims[1], dims[2], ord.periodic, sp->cells, sp->inv, sp->adj, (int32_t)n,
-        sp->adj_ld, (int32_t)ld);
+        dims[0], dims[1], dims[2], ord.periodic, sp->cells, sp->inv, *links, (int32_t)n,
+        (int32_t)ld);
   }
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -344,7 +383,10 @@ extern "C" int lbm_sparse_info(const lbm_sparse* sp, int64_t* n_fluid, const int
   if (!sp || sp->magic != kMagicSparse) return fail(LBM_EINVAL, "not a sparse handle");
   if (n_fluid) *n_fluid = sp->n;
   if (cells_dev) *cells_dev = sp->cells;
-  if (adj_dev) *adj_dev = sp->adj;
+  if (adj_dev) {
+    const int rc = public_links(sp, adj_dev);
+    if (rc != LBM_OK) return rc;
+  }
   if (inv_dev) *inv_dev = sp->inv;
   return LBM_OK;
 }

@@ -604,9 +604,13 @@ extern "C" int lbm_state_create_batched(const lbm_sparse* const* beds, int32_t n
   if (!out) return fail(LBM_EINVAL, "out is NULL");
   *out = nullptr;
   if (!beds || n_beds < 1) return fail(LBM_EINVAL, "need at least one bed");
-  for (int i = 0; i < n_beds; ++i)
+  for (int i = 0; i < n_beds; ++i) {
     if (!beds[i] || beds[i]->magic != kMagicSparse)
       return fail(LBM_EINVAL, "beds[%d] is not a sparse handle", i);
+    // the concatenation copies each bed's public links
+    const int rc = public_links(beds[i], nullptr);
+    if (rc != LBM_OK) return rc;
+  }
   const cudaStream_t stream = beds[0]->stream;
   std::vector<int64_t> begin(n_beds), count(n_beds);
   int64_t total = 0;

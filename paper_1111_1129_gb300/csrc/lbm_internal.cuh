@@ -175,8 +175,20 @@ __host__ __device__ inline uint64_t key_of(const KeySpace& ks, int64_t x, int64_
 // the box (the key space of blocked and Morton orders has gaps).
 __host__ __device__ inline bool cell_of(const KeySpace& ks, uint64_t k, int64_t& x, int64_t& y,
                                         int64_t& z) {
+  // Keys, block sizes and block counts below 2^32 (every lexicographic key
+  // of a box below 2^31 cells) take 32-bit division, several times cheaper
+  // on the GPU than 64-bit division; the results are the same.
+  constexpr uint64_t k32 = 1ull << 32;
   switch (ks.kind) {
     case LBM_ORDER_LEX: {
+      if (k < k32) {
+        const uint32_t kk = (uint32_t)k, nx = (uint32_t)ks.nx, ny = (uint32_t)ks.ny;
+        const uint32_t t = kk / nx;
+        x = (int64_t)(kk - t * nx);
+        y = (int64_t)(t % ny);
+        z = (int64_t)(t / ny);
+        break;
+      }
       x = (int64_t)(k % (uint64_t)ks.nx);
       const uint64_t t = k / (uint64_t)ks.nx;
       y = (int64_t)(t % (uint64_t)ks.ny);
@@ -185,6 +197,17 @@ __host__ __device__ inline bool cell_of(const KeySpace& ks, uint64_t k, int64_t&
     }
     case LBM_ORDER_BLOCKED: {
       const uint64_t bsz = (uint64_t)(ks.bx * ks.by * ks.bz);
+      if (k < k32 && bsz < k32 && (uint64_t)(ks.bx * ks.by) < k32 &&
+          (uint64_t)(ks.nbx * ks.nby) < k32) {
+        const uint32_t kk = (uint32_t)k, b = (uint32_t)bsz, bx = (uint32_t)ks.bx,
+                       by = (uint32_t)ks.by, nbx = (uint32_t)ks.nbx, nby = (uint32_t)ks.nby;
+        const uint32_t blk = kk / b, loc = kk - blk * b;
+        const uint32_t lyz = loc / bx, biyz = blk / nbx;
+        x = (int64_t)(blk - biyz * nbx) * ks.bx + (int64_t)(loc - lyz * bx);
+        y = (int64_t)(biyz % nby) * ks.by + (int64_t)(lyz % by);
+        z = (int64_t)(biyz / nby) * ks.bz + (int64_t)(loc / (bx * by));
+        break;
+      }
       const uint64_t blk = k / bsz, loc = k % bsz;
       const int64_t lx = (int64_t)(loc % (uint64_t)ks.bx);
       const int64_t ly = (int64_t)((loc / (uint64_t)ks.bx) % (uint64_t)ks.by);
@@ -242,7 +265,10 @@ struct lbm_sparse {
   int64_t n;
   int32_t* cells;  // [n]
   int32_t* inv;    // [box]
-  int32_t* adj;    // [18 * n], source slot q n + m (the layout lbm_sparse_info presents)
+  // [18 * n], source slot q n + m (the layout lbm_sparse_info presents).
+  // When ld != n the assembly writes adj_ld only, and adj is derived from
+  // it on first request (public_links); null until then.
+  int32_t* adj;
   // Row stride of the state arrays: n rounded up to kRowAlign (a batch: its
   // padded total).  adj_ld holds the links in that layout, rows of ld
   // entries naming slot r ld + m; null when ld == n (adj serves).
@@ -263,6 +289,9 @@ constexpr int64_t kRowAlign = 64;
 inline int64_t row_stride(int64_t n) { return (n + kRowAlign - 1) / kRowAlign * kRowAlign; }
 // The links the sweeps of a state on sp read: rows of sp->ld entries.
 inline const int32_t* state_links(const lbm_sparse* sp) { return sp->adj_ld ? sp->adj_ld : sp->adj; }
+// The public links of sp (*out may be null), built from adj_ld on the first
+// request and kept (one kernel on sp's stream, which is then synchronised).
+int public_links(const lbm_sparse* sp, const int32_t** out);
 }  // namespace lbm
 
 namespace lbm {
@@ -358,7 +387,7 @@ struct lbm_state {
   int64_t* alpha_fx;   // LBM_F64X with damping: [2][n] alpha 2^63 (-1: the cell takes the
                        // IEEE path) and e 2^63, e = (alpha/2) / (1 + alpha/2)
   double* partials;    // [nblocks * kWarpsPerBlock * 4] FP64 warp sums of the last step,
-                       // then [nblocks * 4] block values formed by lbm_reduce_flux
+                       // then [nblocks * 4] room for the group values of lbm_reduce_flux
   int64_t nblocks;
   bool one_wave;       // nblocks <= 4 x SMs: plain FP32/16-bit steps load links first
   double* red_dev;     // [4] final sums

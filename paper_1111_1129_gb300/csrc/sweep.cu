@@ -555,10 +555,12 @@ extern "C" int lbm_reduce_flux(lbm_state* st, int32_t axis, double* mass_out, do
   const cudaStream_t stream = st->sp->stream;
   const int64_t n = st->sp->n;
   if (n > 0) {
-    double* blocks = st->partials + 4 * kWarpsPerBlock * st->nblocks;
-    collapse_warp_sums_kernel<<<(unsigned)((st->nblocks + 255) / 256), 256, 0, stream>>>(
-        st->partials, st->nblocks, blocks);
-    final_sum_kernel<<<1, 1024, 0, stream>>>(blocks, st->nblocks, st->red_dev);
+    // group sums after the warp slots (room for nblocks values of 4)
+    double* groups = st->partials + 4 * kWarpsPerBlock * st->nblocks;
+    const int64_t ngroups = (st->nblocks + kCollapseThreads - 1) / kCollapseThreads;
+    collapse_warp_sums_kernel<<<(unsigned)ngroups, kCollapseThreads, 0, stream>>>(
+        st->partials, st->nblocks, groups);
+    final_sum_kernel<<<1, 1024, 0, stream>>>(groups, ngroups, st->red_dev);
     LBM_CUDA_TRY(cudaGetLastError());
     LBM_CUDA_TRY(cudaMemcpyAsync(st->red_host, st->red_dev, sizeof(double) * 4,
                                  cudaMemcpyDeviceToHost, stream));

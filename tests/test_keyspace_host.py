@@ -30,6 +30,21 @@ int main(int argc, char** argv) {
   lbm::KeySpace literal, walk;
   if (lbm::make_key_space(dims, ord, false, &literal) || lbm::make_key_space(dims, ord, true, &walk))
     return 2;
+  if (argc > 8) {   // sampled cells (xorshift64), for boxes too large to walk
+    unsigned long long st = strtoull(argv[9], nullptr, 10) | 1ull;
+    for (int s = 0, ns = atoi(argv[8]); s < ns; ++s) {
+      int64_t p[3];
+      for (int d = 0; d < 3; ++d) {
+        st ^= st << 13; st ^= st >> 7; st ^= st << 17;
+        p[d] = s < 8 ? ((s >> d) & 1) * (dims[d] - 1) : (int64_t)(st % (unsigned long long)dims[d]);
+      }
+      const unsigned long long k = lbm::key_of(walk, p[0], p[1], p[2]);
+      int64_t a, b, c;
+      const bool inside = lbm::cell_of(walk, k, a, b, c);
+      printf("%llu %d\n", k, (int)(inside && a == p[0] && b == p[1] && c == p[2]));
+    }
+    return 0;
+  }
   for (int64_t z = 0; z < dims[2]; ++z)
     for (int64_t y = 0; y < dims[1]; ++y)
       for (int64_t x = 0; x < dims[0]; ++x) {
@@ -70,3 +85,24 @@ def test_keys_and_inverse_match_the_oracle(keytool, kind, block, dims):
     roundtrip = np.array(out[1::2], dtype=int)
     np.testing.assert_array_equal(keys, oracle.keys(kind, dims, block).ravel())
     assert roundtrip.all()
+
+
+@pytest.mark.parametrize("kind,block", [(0, (1, 1, 1)), (1, (1024, 1024, 1024)), (1, (8, 8, 8))])
+def test_inverse_beyond_32_bit_keys(keytool, kind, block):
+    """A 1025^3 box (just below 2^31 cells): the inverse takes 32-bit division
+    for keys below 2^32 and 64-bit division above.  In 1024^3 blocks the
+    key space is 2^33, so the far corner's key is 7 * 2^30; the 8 corners
+    and 20,000 seeded cells must come back from their keys.  (The full walk
+    of the smaller boxes above pins the keys against the oracle.)"""
+    dims = (1025, 1025, 1025)
+    out = subprocess.run([keytool, *map(str, dims), str(kind), *map(str, block), "20008", "12345"],
+                         capture_output=True, text=True, check=True).stdout.split()
+    keys = np.array(out[0::2], dtype=np.uint64)
+    assert np.array(out[1::2], dtype=int).all()
+    if block[0] == 1024:
+        # the plane z = 1024 (4 corners and ~20 sampled cells) lies in the
+        # second layer of blocks: keys 4 * 2^30 and up
+        assert keys.max() == 7 * 2**30 and (keys >= 2**32).sum() >= 4
+    else:
+        assert keys.max() < 2**32
+
