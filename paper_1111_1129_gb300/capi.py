@@ -125,12 +125,13 @@ def lbm_build_sparse(flags: int, dims, ordering: lbm_ordering, stream: int) -> i
     return out.value
 
 
-def lbm_sparse_info(sparse: int):
-    """(n_fluid, cells_dev, adj_dev, inv_dev) as Python ints."""
+def lbm_sparse_info(sparse: int, want_adj: bool = True):
+    """(n_fluid, cells_dev, adj_dev, inv_dev) as Python ints; adj_dev is 0
+    unless want_adj (asking for it may build the public links)."""
     n = ctypes.c_int64()
     cells, adj, inv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
     _check(load().lbm_sparse_info(sparse, ctypes.byref(n), ctypes.byref(cells),
-                                  ctypes.byref(adj), ctypes.byref(inv)))
+                                  ctypes.byref(adj) if want_adj else None, ctypes.byref(inv)))
     return n.value, cells.value or 0, adj.value or 0, inv.value or 0
 
 

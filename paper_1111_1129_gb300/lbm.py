@@ -123,7 +123,9 @@ class SparseLattice:
             flags.data_ptr(), self.dims,
             capi.make_ordering(ORDERINGS[ordering], block, periodic),
             int(self.stream.cuda_stream))
-        self.n, self._cells, self._adj, self._inv = capi.lbm_sparse_info(self._handle)
+        # the public links are built on first request (adjacency())
+        self.n, self._cells, _, self._inv = capi.lbm_sparse_info(self._handle, want_adj=False)
+        self._adj = 0
 
     @property
     def handle(self) -> int:
@@ -134,7 +136,9 @@ class SparseLattice:
         return _borrow(self._cells, (self.n,), "<i4", torch.int32).clone()
 
     def adjacency(self) -> torch.Tensor:
-        """Copy of adj[18, N]."""
+        """Copy of adj[18, N] (slot q N + m)."""
+        if not self._adj:
+            self._adj = capi.lbm_sparse_info(self._handle)[2]
         return _borrow(self._adj, (18, self.n), "<i4", torch.int32).clone()
 
     def inverse(self) -> torch.Tensor:
