@@ -598,24 +598,29 @@ def _l2_copy_ceiling(frac: float = 0.6, copies: int = 50, seconds: float = 1.5):
 
 def run_batch_study(args):
     """256 packed beds (cube sides uniform in {24..96}, sphere radii in
-    [3, 8], forces in [1e-7, 1e-5] along z), FP32 shifted storage: the
-    autotuned batched launch in L2 groups, and as one group under a CUDA
-    graph, against the same beds stepped one by one; per-bed fluxes are
-    compared bit for bit."""
+    [3, 8], forces in [1e-7, 1e-5] along z), in the storage form of
+    --batch-precision (FP32 shifted by default): the autotuned batched
+    launch in L2 groups, and as one group under a CUDA graph, against the
+    same beds stepped one by one; per-bed fluxes are compared bit for bit."""
     import torch
 
-    from paper_1111_1129_gb300 import (BatchedState, LBMState, SparseLattice, capi, inputs,
-                                       omega_minus)
+    from paper_1111_1129_gb300 import (BatchedState, LBMState, SparseLattice, capi,
+                                       deviation_bound, inputs, omega_minus, shifted_scale_exp)
 
     capi.load()
     wm = omega_minus(WP)
+    prec = args.batch_precision
     beds, fz = inputs.batch_beds(256, 0)
     forces = [(0.0, 0.0, float(f)) for f in fz]
+    # 16-bit forms: one scale for all beds, from the largest force and the
+    # widest bed (tube radius at most half the largest cube side, 48)
+    k = shifted_scale_exp(deviation_bound(float(max(abs(fz))), 48.0, WP)) \
+        if prec in ("f16s", "bf16s") else 0
     lats = [SparseLattice(torch.from_numpy(b.flags).cuda(), args.ordering, (8, 8, 8), b.periodic)
             for b in beds]
     n_fluid = sum(l.n for l in lats)
     K = args.batch_steps
-    tuner = BatchedState(lats, "f32s")
+    tuner = BatchedState(lats, prec, k)
     block, cpt, cand = tuner.tune(20, WP, wm, forces)
     tuner.close()
 
@@ -632,7 +637,7 @@ def run_batch_study(args):
     for label, graph, group_bytes in (("batched_l2_groups", True, -1),
                                       ("batched_graph", True, 0),
                                       ("batched_no_graph", False, 0)):
-        bs = BatchedState(lats, "f32s")
+        bs = BatchedState(lats, prec, k)
         bs.configure(block, cpt, graph)
         n_groups = bs.groups(group_bytes)
         bs.step(K, WP, wm, forces)          # warm-up; captures the graph
@@ -645,7 +650,7 @@ def run_batch_study(args):
         else:
             assert list(flux) == list(batched_flux), "grouping changed a bed's flux"
         bs.close()
-    states = [LBMState(l, "f32s") for l in lats]
+    states = [LBMState(l, prec, k) for l in lats]
 
     def separate():
         for st, F in zip(states, forces):
@@ -659,20 +664,23 @@ def run_batch_study(args):
     for l in lats:
         l.close()
     # L2 groups stream from L2: their roofline is an L2 copy ceiling
-    # measured here; 224 algorithmic bytes per update (19 FP32 loads, 19 FP32
-    # stores, 18 int32 links), plus the per-block bed-table reads (chunk's
-    # bed, begin, count, force: 52 bytes per block of block x cells/thread)
+    # measured here; the form's algorithmic bytes per update (19 loads, 19
+    # stores, 18 int32 links; 224 for FP32), plus the per-block bed-table
+    # reads (chunk's bed, begin, count, force: 52 bytes per block of block x
+    # cells/thread)
     l2_gbs, l2_buf, l2_clocks = _l2_copy_ceiling()
-    bpl = 224 + 52 / (block * cpt)
+    bpl = BYTES_PER_LUP[prec] + 52 / (block * cpt)
     achieved = bpl * n_fluid * K / (out["batched_l2_groups"]["ms"] * 1e-3) / 1e9
     roofline = {"bound": "l2", "achieved": achieved, "peak": l2_gbs, "unit": "GB/s",
                 "frac": achieved / l2_gbs, "bytes_per_lup": bpl,
                 "peak_kind": f"measured here: L2-resident copy, 2 x {l2_buf / 1e6:.1f} MB "
                              "FP32 buffers, 50 copies per CUDA graph, best replay of 1.5 s",
-                "peak_clocks": l2_clocks, "kernel": "batch_sweep_kernel<f32s> (L2 groups)"}
+                "peak_clocks": l2_clocks, "kernel": f"batch_sweep_kernel<{prec}> (L2 groups)"}
     line = {"study": "batched beds", "n_beds": 256, "fluid_cells": n_fluid, "steps": K,
             "roofline": roofline,
-            "ordering": args.ordering, "precision": "f32s", "tuned": {"block": block, "cells_per_thread": cpt,
+            "ordering": args.ordering, "precision": prec,
+            "scale_exp": k if prec in ("f16s", "bf16s") else None,
+            "tuned": {"block": block, "cells_per_thread": cpt,
                                            "candidate_ms_block_major": cand},
             **out, "speedup_vs_separate": out["batched_l2_groups"]["mflups"] /
             out["separate_loops"]["mflups"],
@@ -780,6 +788,7 @@ def main():
     ap.add_argument("--batch-study", action="store_true",
                     help="run the 256-bed batching study instead of the benchmark")
     ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--batch-precision", default="f32s", choices=list(BYTES_PER_LUP))
     ap.add_argument("--ordering-study", action="store_true",
                     help="run the numbering-scheme study instead of the benchmark")
     ap.add_argument("--study-forms", default="f64x,f32s,f16s")

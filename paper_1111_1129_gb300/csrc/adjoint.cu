@@ -55,11 +55,18 @@ struct lbm_adjoint {
 namespace lbm {
 namespace {
 
+// Coefficients of the reverse step, for its two forms (adjoint_step_kernel):
+// the weighted form, and the pair form, which carries the weighted moments
+// M of the adjoint as M' = 36 M (w0 = 12/36, w1 = 2/36, w2 = 1/36) with the
+// 1/36 in the coefficients that multiply them.
 template <class C>
 struct AdjCoef {
   C wp, one_m_wp;  // w+, 1 - w+
   C k1, k2;        // 1 - (w+ + w-)/2, (w- - w+)/2
   C wm, src;       // w-, 1 - w-/2
+  C hp, hm;        // (1 - w+)/2, (1 - w-)/2: the pair form of L^T
+  C wp36, wp12, wp4;   // w+/36 (base), 3 w+/36, 9 w+/36 (G)
+  C wm12, src12;   // beta/36 = w-/12 - alpha src/12
   C inv_n;         // 1 / N
 };
 
@@ -72,6 +79,13 @@ AdjCoef<C> make_adj_coef(double wp, double wm, int64_t n) {
   a.k2 = (C)(0.5 * (wm - wp));
   a.wm = (C)wm;
   a.src = (C)(1.0 - 0.5 * wm);
+  a.hp = (C)(0.5 * (1.0 - wp));
+  a.hm = (C)(0.5 * (1.0 - wm));
+  a.wp36 = (C)(wp / 36.0);
+  a.wp12 = (C)(wp / 12.0);
+  a.wp4 = (C)(0.25 * wp);
+  a.wm12 = (C)(wm / 12.0);
+  a.src12 = (C)((1.0 - 0.5 * wm) / 12.0);
   a.inv_n = (C)(n > 0 ? 1.0 / (double)n : 0.0);
   return a;
 }
@@ -191,55 +205,110 @@ __global__ void __launch_bounds__(kSweepThreads)
     C u[3], s;
     const C al = DAMPED ? alpha[i] : C(0);
     velocity<C, DAMPED>(g, k, al, u, s);
-    // weighted moments of the adjoint
     C S[9], D[9];
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
       S[p] = lf[2 * p + 1] + lf[2 * p + 2];
       D[p] = lf[2 * p + 1] - lf[2 * p + 2];
     }
-    const C w0 = C(1.0 / 3.0), w1 = C(1.0 / 18.0), w2 = C(1.0 / 36.0);
-    const C M0 = w0 * lf[0] + w1 * (S[0] + S[1] + S[2]) +
-                 w2 * (((S[3] + S[4]) + (S[5] + S[6])) + (S[7] + S[8]));
-    const C M1x = w1 * D[0] + w2 * ((D[3] + D[4]) + (D[5] + D[6]));
-    const C M1y = w1 * D[1] + w2 * ((D[3] - D[4]) + (D[7] + D[8]));
-    const C M1z = w1 * D[2] + w2 * ((D[5] - D[6]) + (D[7] - D[8]));
-    const C Mxx = w1 * S[0] + w2 * ((S[3] + S[4]) + (S[5] + S[6]));
-    const C Myy = w1 * S[1] + w2 * ((S[3] + S[4]) + (S[7] + S[8]));
-    const C Mzz = w1 * S[2] + w2 * ((S[5] + S[6]) + (S[7] + S[8]));
-    const C Mxy = w2 * (S[3] - S[4]);
-    const C Mxz = w2 * (S[5] - S[6]);
-    const C Myz = w2 * (S[7] - S[8]);
-    const C nine_wp = C(9) * a.wp, three_wp_m0 = C(3) * a.wp * M0;
-    const C beta = C(3) * (a.wm - al * a.src);
-    const C Gx = nine_wp * (Mxx * u[0] + Mxy * u[1] + Mxz * u[2]) - three_wp_m0 * u[0] + beta * M1x;
-    const C Gy = nine_wp * (Mxy * u[0] + Myy * u[1] + Myz * u[2]) - three_wp_m0 * u[1] + beta * M1y;
-    const C Gz = nine_wp * (Mxz * u[0] + Myz * u[1] + Mzz * u[2]) - three_wp_m0 * u[2] + beta * M1z;
-    const C base = a.wp * M0;
-    lam_out[i] = a.one_m_wp * lf[0] + base;
+    // Two forms of the same update.  FP64 arithmetic takes the pair form:
+    // the outputs of pair (a, b) are e +- o, e = (1 - w+)/2 S + base and
+    // o = (1 - w-)/2 D + s G (L^T's k1 la + k2 lb and k1 lb + k2 la have sum
+    // (1 - w+) S and difference (1 - w-) D), with the moments carried as
+    // 36 M.  It issues about a quarter fewer FP64 instructions: on the damped
+    // 128^3 bed the IEEE reverse step took 371 us against 448 and the
+    // reverse pass 1,297 ms against 1,450.  FP32 arithmetic keeps the
+    // weighted form: there the pair form took 40 registers instead of 48,
+    // ran 6 blocks per SM instead of 5, and was slower, 57.6 us against 53.2
+    // (DRAM 65% against 71%; reverse pass 187 ms against 178).
+    if constexpr (sizeof(C) == 8) {
+      const C s34 = S[3] + S[4], s56 = S[5] + S[6], s78 = S[7] + S[8];
+      const C M0 = C(12) * lf[0] + C(2) * ((S[0] + S[1]) + S[2]) + ((s34 + s56) + s78);
+      const C M1x = C(2) * D[0] + ((D[3] + D[4]) + (D[5] + D[6]));
+      const C M1y = C(2) * D[1] + ((D[3] - D[4]) + (D[7] + D[8]));
+      const C M1z = C(2) * D[2] + ((D[5] - D[6]) + (D[7] - D[8]));
+      const C Mxx = C(2) * S[0] + (s34 + s56);
+      const C Myy = C(2) * S[1] + (s34 + s78);
+      const C Mzz = C(2) * S[2] + (s56 + s78);
+      const C Mxy = S[3] - S[4], Mxz = S[5] - S[6], Myz = S[7] - S[8];
+      // G = 9 w+ M2 u - 3 w+ M0 u + beta M1, beta = 3 (w- - alpha (1 - w-/2))
+      const C m0 = a.wp12 * M0;
+      const C beta = a.wm12 - al * a.src12;
+      const C Gx = a.wp4 * (Mxx * u[0] + Mxy * u[1] + Mxz * u[2]) - m0 * u[0] + beta * M1x;
+      const C Gy = a.wp4 * (Mxy * u[0] + Myy * u[1] + Myz * u[2]) - m0 * u[1] + beta * M1y;
+      const C Gz = a.wp4 * (Mxz * u[0] + Myz * u[1] + Mzz * u[2]) - m0 * u[2] + beta * M1z;
+      const C base = a.wp36 * M0;
+      lam_out[i] = a.one_m_wp * lf[0] + base;
+#define LBM_ADJ_PAIR(P, CG)                                                    \
+  {                                                                            \
+    const C e_ = a.hp * S[P] + base;                                           \
+    const C o_ = a.hm * D[P] + s * (CG);                                       \
+    lam_out[(2 * P + 1) * n + i] = e_ + o_;                                    \
+    lam_out[(2 * P + 2) * n + i] = e_ - o_;                                    \
+  }
+      LBM_ADJ_PAIR(0, Gx)
+      LBM_ADJ_PAIR(1, Gy)
+      LBM_ADJ_PAIR(2, Gz)
+      LBM_ADJ_PAIR(3, Gx + Gy)
+      LBM_ADJ_PAIR(4, Gx - Gy)
+      LBM_ADJ_PAIR(5, Gx + Gz)
+      LBM_ADJ_PAIR(6, Gx - Gz)
+      LBM_ADJ_PAIR(7, Gy + Gz)
+      LBM_ADJ_PAIR(8, Gy - Gz)
+#undef LBM_ADJ_PAIR
+      // dJ/dF += (s/2) G + 3 (1 - w-/2) M1; dJ/dalpha += -(s/2) G.u - 3 (1 - w-/2) M1.u
+      const C hs = C(0.5) * s;
+      red[0] = hs * Gx + a.src12 * M1x;
+      red[1] = hs * Gy + a.src12 * M1y;
+      red[2] = hs * Gz + a.src12 * M1z;
+      const C Gu = Gx * u[0] + Gy * u[1] + Gz * u[2];
+      const C M1u = M1x * u[0] + M1y * u[1] + M1z * u[2];
+      dalpha[i] += (double)(-hs * Gu - a.src12 * M1u);
+    } else {
+      // weighted moments of the adjoint
+      const C w0 = C(1.0 / 3.0), w1 = C(1.0 / 18.0), w2 = C(1.0 / 36.0);
+      const C M0 = w0 * lf[0] + w1 * (S[0] + S[1] + S[2]) +
+                   w2 * (((S[3] + S[4]) + (S[5] + S[6])) + (S[7] + S[8]));
+      const C M1x = w1 * D[0] + w2 * ((D[3] + D[4]) + (D[5] + D[6]));
+      const C M1y = w1 * D[1] + w2 * ((D[3] - D[4]) + (D[7] + D[8]));
+      const C M1z = w1 * D[2] + w2 * ((D[5] - D[6]) + (D[7] - D[8]));
+      const C Mxx = w1 * S[0] + w2 * ((S[3] + S[4]) + (S[5] + S[6]));
+      const C Myy = w1 * S[1] + w2 * ((S[3] + S[4]) + (S[7] + S[8]));
+      const C Mzz = w1 * S[2] + w2 * ((S[5] + S[6]) + (S[7] + S[8]));
+      const C Mxy = w2 * (S[3] - S[4]);
+      const C Mxz = w2 * (S[5] - S[6]);
+      const C Myz = w2 * (S[7] - S[8]);
+      const C nine_wp = C(9) * a.wp, three_wp_m0 = C(3) * a.wp * M0;
+      const C beta = C(3) * (a.wm - al * a.src);
+      const C Gx = nine_wp * (Mxx * u[0] + Mxy * u[1] + Mxz * u[2]) - three_wp_m0 * u[0] + beta * M1x;
+      const C Gy = nine_wp * (Mxy * u[0] + Myy * u[1] + Myz * u[2]) - three_wp_m0 * u[1] + beta * M1y;
+      const C Gz = nine_wp * (Mxz * u[0] + Myz * u[1] + Mzz * u[2]) - three_wp_m0 * u[2] + beta * M1z;
+      const C base = a.wp * M0;
+      lam_out[i] = a.one_m_wp * lf[0] + base;
 #define LBM_ADJ_PAIR(P, CG)                                                    \
   {                                                                            \
     const C sg_ = s * (CG);                                                    \
     lam_out[(2 * P + 1) * n + i] = a.k1 * lf[2 * P + 1] + a.k2 * lf[2 * P + 2] + base + sg_; \
     lam_out[(2 * P + 2) * n + i] = a.k1 * lf[2 * P + 2] + a.k2 * lf[2 * P + 1] + base - sg_; \
   }
-    LBM_ADJ_PAIR(0, Gx)
-    LBM_ADJ_PAIR(1, Gy)
-    LBM_ADJ_PAIR(2, Gz)
-    LBM_ADJ_PAIR(3, Gx + Gy)
-    LBM_ADJ_PAIR(4, Gx - Gy)
-    LBM_ADJ_PAIR(5, Gx + Gz)
-    LBM_ADJ_PAIR(6, Gx - Gz)
-    LBM_ADJ_PAIR(7, Gy + Gz)
-    LBM_ADJ_PAIR(8, Gy - Gz)
+      LBM_ADJ_PAIR(0, Gx)
+      LBM_ADJ_PAIR(1, Gy)
+      LBM_ADJ_PAIR(2, Gz)
+      LBM_ADJ_PAIR(3, Gx + Gy)
+      LBM_ADJ_PAIR(4, Gx - Gy)
+      LBM_ADJ_PAIR(5, Gx + Gz)
+      LBM_ADJ_PAIR(6, Gx - Gz)
+      LBM_ADJ_PAIR(7, Gy + Gz)
+      LBM_ADJ_PAIR(8, Gy - Gz)
 #undef LBM_ADJ_PAIR
-    const C hs = C(0.5) * s, three_src = C(3) * a.src;
-    red[0] = hs * Gx + three_src * M1x;
-    red[1] = hs * Gy + three_src * M1y;
-    red[2] = hs * Gz + three_src * M1z;
-    const C Gu = Gx * u[0] + Gy * u[1] + Gz * u[2];
-    const C M1u = M1x * u[0] + M1y * u[1] + M1z * u[2];
-    dalpha[i] += (double)(-hs * Gu - three_src * M1u);
+      const C hs = C(0.5) * s, three_src = C(3) * a.src;
+      red[0] = hs * Gx + three_src * M1x;
+      red[1] = hs * Gy + three_src * M1y;
+      red[2] = hs * Gz + three_src * M1z;
+      const C Gu = Gx * u[0] + Gy * u[1] + Gz * u[2];
+      const C M1u = M1x * u[0] + M1y * u[1] + M1z * u[2];
+      dalpha[i] += (double)(-hs * Gu - three_src * M1u);
+    }
   }
   block_accumulate4(red, part + z + 4 * (int64_t)blockIdx.x, false);
 }
@@ -300,32 +369,23 @@ __device__ __forceinline__ ds ds_from_fixed(int64_t v, int sc) {
   return {r.hi * scale, r.lo * scale};
 }
 
-// Coefficients of the reverse step as pairs.
+// Coefficients of the reverse step as pairs (those of AdjCoef).
 struct AdjCoefDS {
-  ds wp, one_m_wp, k1, k2, three_wm, src, three_src, nine_wp, three_wp, inv_n;
-  ds w0, w1, w2, hF[3];
+  ds one_m_wp, hp, hm, wp36, wp12, wp4, wm12, src12;
   int64_t fhF[3];   // F/2 in units 2^-58, for the fixed-point velocity
 };
 
-AdjCoefDS make_adj_coef_ds(double wp, double wm, const double F[3], int64_t n) {
+AdjCoefDS make_adj_coef_ds(double wp, double wm, const double F[3]) {
   AdjCoefDS a;
-  a.wp = ds_from_double(wp);
   a.one_m_wp = ds_from_double(1.0 - wp);
-  a.k1 = ds_from_double(1.0 - 0.5 * (wp + wm));
-  a.k2 = ds_from_double(0.5 * (wm - wp));
-  a.three_wm = ds_from_double(3.0 * wm);
-  a.src = ds_from_double(1.0 - 0.5 * wm);
-  a.three_src = ds_from_double(3.0 * (1.0 - 0.5 * wm));
-  a.nine_wp = ds_from_double(9.0 * wp);
-  a.three_wp = ds_from_double(3.0 * wp);
-  a.inv_n = ds_from_double(n > 0 ? 1.0 / (double)n : 0.0);
-  a.w0 = ds_from_double(1.0 / 3.0);
-  a.w1 = ds_from_double(1.0 / 18.0);
-  a.w2 = ds_from_double(1.0 / 36.0);
-  for (int d = 0; d < 3; ++d) {
-    a.hF[d] = ds_from_double(0.5 * F[d]);
-    a.fhF[d] = (int64_t)std::llround(0.5 * F[d] * 0x1p58);
-  }
+  a.hp = ds_from_double(0.5 * (1.0 - wp));
+  a.hm = ds_from_double(0.5 * (1.0 - wm));
+  a.wp36 = ds_from_double(wp / 36.0);
+  a.wp12 = ds_from_double(wp / 12.0);
+  a.wp4 = ds_from_double(0.25 * wp);
+  a.wm12 = ds_from_double(wm / 12.0);
+  a.src12 = ds_from_double((1.0 - 0.5 * wm) / 12.0);
+  for (int d = 0; d < 3; ++d) a.fhF[d] = (int64_t)std::llround(0.5 * F[d] * 0x1p58);
   return a;
 }
 
@@ -468,48 +528,52 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_ADJ_DS_MIN_BLOCKS)
     ds lf[19];
 #pragma unroll
     for (int q = 0; q < 19; ++q) lf[q] = {l2[q].x, l2[q].y};
+    // moments carried as 36 M, as in adjoint_step_kernel; the scalings by
+    // 2, 4 and 8 are exact
     ds S[9], D[9];
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
       S[p] = ds_add(lf[2 * p + 1], lf[2 * p + 2]);
       D[p] = ds_sub(lf[2 * p + 1], lf[2 * p + 2]);
     }
-    const ds M0 = ds_add(ds_add(ds_mul(a.w0, lf[0]), ds_mul(a.w1, ds_add(ds_add(S[0], S[1]), S[2]))),
-                         ds_mul(a.w2, ds_add(ds_add(ds_add(S[3], S[4]), ds_add(S[5], S[6])),
-                                             ds_add(S[7], S[8]))));
-    const ds M1x = ds_add(ds_mul(a.w1, D[0]), ds_mul(a.w2, ds_add(ds_add(D[3], D[4]), ds_add(D[5], D[6]))));
-    const ds M1y = ds_add(ds_mul(a.w1, D[1]), ds_mul(a.w2, ds_add(ds_sub(D[3], D[4]), ds_add(D[7], D[8]))));
-    const ds M1z = ds_add(ds_mul(a.w1, D[2]), ds_mul(a.w2, ds_add(ds_sub(D[5], D[6]), ds_sub(D[7], D[8]))));
-    const ds Mxx = ds_add(ds_mul(a.w1, S[0]), ds_mul(a.w2, ds_add(ds_add(S[3], S[4]), ds_add(S[5], S[6]))));
-    const ds Myy = ds_add(ds_mul(a.w1, S[1]), ds_mul(a.w2, ds_add(ds_add(S[3], S[4]), ds_add(S[7], S[8]))));
-    const ds Mzz = ds_add(ds_mul(a.w1, S[2]), ds_mul(a.w2, ds_add(ds_add(S[5], S[6]), ds_add(S[7], S[8]))));
-    const ds Mxy = ds_mul(a.w2, ds_sub(S[3], S[4]));
-    const ds Mxz = ds_mul(a.w2, ds_sub(S[5], S[6]));
-    const ds Myz = ds_mul(a.w2, ds_sub(S[7], S[8]));
-    const ds three_wp_m0 = ds_mul(a.three_wp, M0);
-    // beta = 3 (w- - alpha (1 - w-/2)); alpha from its fixed-point value
-    ds beta = a.three_wm;
+    const ds s34 = ds_add(S[3], S[4]), s56 = ds_add(S[5], S[6]), s78 = ds_add(S[7], S[8]);
+    const ds M0 = ds_add(ds_add(ds_add(ds_scale_pow2(lf[0], 8.f), ds_scale_pow2(lf[0], 4.f)),
+                                ds_scale_pow2(ds_add(ds_add(S[0], S[1]), S[2]), 2.f)),
+                         ds_add(ds_add(s34, s56), s78));
+    const ds M1x = ds_add(ds_scale_pow2(D[0], 2.f), ds_add(ds_add(D[3], D[4]), ds_add(D[5], D[6])));
+    const ds M1y = ds_add(ds_scale_pow2(D[1], 2.f), ds_add(ds_sub(D[3], D[4]), ds_add(D[7], D[8])));
+    const ds M1z = ds_add(ds_scale_pow2(D[2], 2.f), ds_add(ds_sub(D[5], D[6]), ds_sub(D[7], D[8])));
+    const ds Mxx = ds_add(ds_scale_pow2(S[0], 2.f), ds_add(s34, s56));
+    const ds Myy = ds_add(ds_scale_pow2(S[1], 2.f), ds_add(s34, s78));
+    const ds Mzz = ds_add(ds_scale_pow2(S[2], 2.f), ds_add(s56, s78));
+    const ds Mxy = ds_sub(S[3], S[4]);
+    const ds Mxz = ds_sub(S[5], S[6]);
+    const ds Myz = ds_sub(S[7], S[8]);
+    const ds m0 = ds_mul(a.wp12, M0);
+    // beta/36 = w-/12 - alpha src/12; alpha from its fixed-point value
+    ds beta = a.wm12;
     if constexpr (DAMPED) {
       const int64_t A = __ldg(alpha_fx + i);
       const ds al = A >= 0 ? ds_from_fixed(A, 63) : ds_from_double(alpha[i]);
-      beta = ds_sub(beta, ds_mul(a.three_src, al));
+      beta = ds_sub(beta, ds_mul(a.src12, al));
     }
-    const ds Gx = ds_add(ds_sub(ds_mul(a.nine_wp, ds_add(ds_add(ds_mul(Mxx, u[0]), ds_mul(Mxy, u[1])), ds_mul(Mxz, u[2]))),
-                                ds_mul(three_wp_m0, u[0])), ds_mul(beta, M1x));
-    const ds Gy = ds_add(ds_sub(ds_mul(a.nine_wp, ds_add(ds_add(ds_mul(Mxy, u[0]), ds_mul(Myy, u[1])), ds_mul(Myz, u[2]))),
-                                ds_mul(three_wp_m0, u[1])), ds_mul(beta, M1y));
-    const ds Gz = ds_add(ds_sub(ds_mul(a.nine_wp, ds_add(ds_add(ds_mul(Mxz, u[0]), ds_mul(Myz, u[1])), ds_mul(Mzz, u[2]))),
-                                ds_mul(three_wp_m0, u[2])), ds_mul(beta, M1z));
-    const ds base = ds_mul(a.wp, M0);
+    const ds Gx = ds_add(ds_sub(ds_mul(a.wp4, ds_add(ds_add(ds_mul(Mxx, u[0]), ds_mul(Mxy, u[1])), ds_mul(Mxz, u[2]))),
+                                ds_mul(m0, u[0])), ds_mul(beta, M1x));
+    const ds Gy = ds_add(ds_sub(ds_mul(a.wp4, ds_add(ds_add(ds_mul(Mxy, u[0]), ds_mul(Myy, u[1])), ds_mul(Myz, u[2]))),
+                                ds_mul(m0, u[1])), ds_mul(beta, M1y));
+    const ds Gz = ds_add(ds_sub(ds_mul(a.wp4, ds_add(ds_add(ds_mul(Mxz, u[0]), ds_mul(Myz, u[1])), ds_mul(Mzz, u[2]))),
+                                ds_mul(m0, u[2])), ds_mul(beta, M1z));
+    const ds base = ds_mul(a.wp36, M0);
     {
       const ds v = ds_add(ds_mul(a.one_m_wp, lf[0]), base);
       lam_out[i] = make_float2(v.hi, v.lo);
     }
 #define LBM_ADJ_DS_PAIR(P, CG)                                                                  \
   {                                                                                             \
-    const ds sg_ = ds_mul(s, (CG));                                                             \
-    const ds va_ = ds_add(ds_add(ds_add(ds_mul(a.k1, lf[2 * P + 1]), ds_mul(a.k2, lf[2 * P + 2])), base), sg_); \
-    const ds vb_ = ds_sub(ds_add(ds_add(ds_mul(a.k1, lf[2 * P + 2]), ds_mul(a.k2, lf[2 * P + 1])), base), sg_); \
+    const ds e_ = ds_add(ds_mul(a.hp, S[P]), base);                                             \
+    const ds o_ = ds_add(ds_mul(a.hm, D[P]), ds_mul(s, (CG)));                                  \
+    const ds va_ = ds_add(e_, o_);                                                              \
+    const ds vb_ = ds_sub(e_, o_);                                                              \
     lam_out[(2 * P + 1) * n + i] = make_float2(va_.hi, va_.lo);                                \
     lam_out[(2 * P + 2) * n + i] = make_float2(vb_.hi, vb_.lo);                                \
   }
@@ -524,12 +588,12 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_ADJ_DS_MIN_BLOCKS)
     LBM_ADJ_DS_PAIR(8, ds_sub(Gy, Gz))
 #undef LBM_ADJ_DS_PAIR
     const ds hs = ds_scale_pow2(s, 0.5f);
-    red[0] = ds_add(ds_mul(hs, Gx), ds_mul(a.three_src, M1x));
-    red[1] = ds_add(ds_mul(hs, Gy), ds_mul(a.three_src, M1y));
-    red[2] = ds_add(ds_mul(hs, Gz), ds_mul(a.three_src, M1z));
+    red[0] = ds_add(ds_mul(hs, Gx), ds_mul(a.src12, M1x));
+    red[1] = ds_add(ds_mul(hs, Gy), ds_mul(a.src12, M1y));
+    red[2] = ds_add(ds_mul(hs, Gz), ds_mul(a.src12, M1z));
     const ds Gu = ds_add(ds_add(ds_mul(Gx, u[0]), ds_mul(Gy, u[1])), ds_mul(Gz, u[2]));
     const ds M1u = ds_add(ds_add(ds_mul(M1x, u[0]), ds_mul(M1y, u[1])), ds_mul(M1z, u[2]));
-    dalpha[i] += ds_to_double(ds_neg(ds_add(ds_mul(hs, Gu), ds_mul(a.three_src, M1u))));
+    dalpha[i] += ds_to_double(ds_neg(ds_add(ds_mul(hs, Gu), ds_mul(a.src12, M1u))));
   }
   block_accumulate4_ds(red, part + 4 * (int64_t)blockIdx.x, false);
 }
@@ -593,7 +657,7 @@ struct Runner {
     a = make_adj_coef<C>(ad->wp, ad->wm, n);
     alpha = (const C*)st->alpha;
     state_elems = 19 * (size_t)n;
-    if constexpr (PREC == LBM_F64X) ads = make_adj_coef_ds(ad->wp, ad->wm, ad->F, n);
+    if constexpr (PREC == LBM_F64X) ads = make_adj_coef_ds(ad->wp, ad->wm, ad->F);
   }
   float2* lam2(int i) const { return (float2*)ad->lam[i]; }
   S* ckpt(int j) const { return (S*)ad->ckpt + (size_t)j * state_elems; }
