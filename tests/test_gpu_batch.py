@@ -39,7 +39,7 @@ def _lattices(beds):
             for b in beds]
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32s", "f16s"])
+@pytest.mark.parametrize("precision", ["f64", "f32s", "f16s", "bf16s"])
 def test_batched_beds_bit_identical_to_separate_runs(precision):
     beds, forces = _beds()
     lats = _lattices(beds)
@@ -55,7 +55,7 @@ def test_batched_beds_bit_identical_to_separate_runs(precision):
     for block, cpt, graph, group_bytes in [(256, 1, True, 0), (128, 4, True, 0),
                                            (512, 2, False, 0), (512, 4, True, 0),
                                            (256, 1, True, 1), (256, 2, True, 3 << 20),
-                                           (512, 4, False, 1 << 20)]:
+                                           (128, 2, True, 1), (512, 4, False, 1 << 20)]:
         bs = BatchedState(lats, precision, 20)
         bs.configure(block, cpt, graph)
         n_groups = bs.groups(group_bytes)
