@@ -111,13 +111,16 @@ def test_orderings_bitwise_identical():
         lat.close()
 
 
-def test_large_bed_sampled_parity():
-    """1024x256x256 bed, 8^3 blocked order, the benchmark's launch shape:
-    one step checked cell by cell with the oracle's collision on a sample,
-    and the stored mass unchanged exactly after 50 steps."""
+@pytest.mark.parametrize("ordering", ["lex", "blocked"])
+def test_large_bed_sampled_parity(ordering):
+    """1024x256x256 bed in lexicographic order (the benchmark's launch
+    configuration) and 8^3 blocked order: one step checked cell by cell
+    with the oracle's collision on a sample, and the stored mass unchanged
+    exactly after 50 steps."""
     bed = inputs.bed_large(0)
-    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "blocked", (8, 8, 8), bed.periodic)
-    cells, _, adj = oracle.build_sparse(bed.flags, oracle.ORDER_BLOCKED, (8, 8, 8), bed.periodic)
+    kind = {"lex": oracle.ORDER_LEX, "blocked": oracle.ORDER_BLOCKED}[ordering]
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), ordering, (8, 8, 8), bed.periodic)
+    cells, _, adj = oracle.build_sparse(bed.flags, kind, (8, 8, 8), bed.periodic)
     np.testing.assert_array_equal(lat.cells().cpu().numpy(), cells)
     st = LBMState(lat, "f64x")
     F = (1e-6, 0.0, 0.0)
@@ -135,7 +138,7 @@ def test_large_bed_sampled_parity():
         ref[:, j], _, _ = oracle.collide(g, F, 0.0, WP, WM)
     # a few ulp of the rest population (~0.33, ulp 5.6e-17): it takes the
     # rounding of rho and the oracle rounds too
-    fp64_measures.check(nxt[:, sample], ref, 1, label="f64x large bed, one step, 2000 cells")
+    fp64_measures.check(nxt[:, sample], ref, 1, label=f"f64x large bed {ordering}, one step, 2000 cells")
     st.close()
     lat.close()
 

@@ -71,3 +71,52 @@ def test_pair_steps_equal_single_cell_steps(flags, precision, damped, ordering):
     assert torch.equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1]
     lat.close()
+
+
+def test_large_bed_pair_steps_and_one_step_parity():
+    """The 1024x256x256 bed at full size in the benchmark's configuration
+    (lexicographic order, FP16 shifted at the benchmark's scale): two steps
+    in one call (the pair kernel, then the one-cell reducing step) equal two
+    one-step calls (the one-cell kernel each) bit for bit, and one step from
+    the stored state matches the oracle's collision on 2000 sampled cells
+    within one storage unit."""
+    import oracle
+    from paper_1111_1129_gb300 import deviation_bound, shifted_scale_exp
+    from storage_units import W, one_step_tolerance
+
+    bed = inputs.bed_large(0)
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "lex", (8, 8, 8), bed.periodic)
+    assert lat.n > 4 * 152 * 256 and lat.n % 64 != 0   # many waves; padded rows
+    F = (1e-6, 0.0, 0.0)
+    k = shifted_scale_exp(deviation_bound(F[0], 125.0, WP))
+    a = LBMState(lat, "f16s", k)
+    a.step(30, WP, WM, F)
+    f30 = a.get_pdfs()
+    b = LBMState(lat, "f16s", k)
+    b.set_pdfs(f30)
+    assert torch.equal(b.get_pdfs(), f30)      # decode and encode are exact
+    a.step(2, WP, WM, F)
+    b.step(1, WP, WM, F)
+    b.step(1, WP, WM, F)
+    assert torch.equal(a.get_pdfs(), b.get_pdfs())
+    assert a.reduce_flux(0) == b.reduce_flux(0)
+    a.close()
+    # one step from f30 against the oracle's collision of the oracle's pull
+    b.set_pdfs(f30)
+    b.step(1, WP, WM, F)
+    nxt = b.get_pdfs().cpu().numpy()
+    b.close()
+    cells, _, adj = oracle.build_sparse(bed.flags, oracle.ORDER_LEX, periodic=bed.periodic)
+    np.testing.assert_array_equal(lat.cells().cpu().numpy(), cells)
+    prev = f30.cpu().numpy()
+    flat = prev.ravel()
+    sample = np.random.default_rng(2).choice(lat.n, 2000, replace=False)
+    ref = np.empty((19, sample.size))
+    for j, n in enumerate(sample):
+        g = np.concatenate([[flat[n]], flat[adj[:, n]]])
+        ref[:, j], _, _ = oracle.collide(g, F, 0.0, WP, WM)
+    tol = one_step_tolerance("f16s", ref, float(np.abs(prev - W[:, None]).max()), k)
+    worst = float((np.abs(nxt[:, sample] - ref) / tol).max())
+    print(f"large bed f16s k={k}: one step, 2000 cells, max err/tol {worst:.3f}")
+    assert worst <= 1.0
+    lat.close()

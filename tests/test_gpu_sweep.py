@@ -250,14 +250,17 @@ def test_step_argument_validation():
     lat.close()
 
 
-def test_large_bed_sampled_parity():
-    """The 1024x256x256 bed at full size, 8^3 blocked order, in the launch
-    configuration the benchmark times: adjacency bit-exact against the
-    oracle, and one step checked cell by cell on a sample with the oracle's
-    collision applied to the oracle's own pull of the GPU's previous state."""
+@pytest.mark.parametrize("ordering", ["lex", "blocked"])
+def test_large_bed_sampled_parity(ordering):
+    """The 1024x256x256 bed at full size, in lexicographic order (the launch
+    configuration the benchmark times) and 8^3 blocked order: adjacency
+    bit-exact against the oracle, and one step checked cell by cell on a
+    sample with the oracle's collision applied to the oracle's own pull of
+    the GPU's previous state."""
     bed = inputs.bed_large(0)
-    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "blocked", (8, 8, 8), bed.periodic)
-    cells, _, adj = oracle.build_sparse(bed.flags, oracle.ORDER_BLOCKED, (8, 8, 8), bed.periodic)
+    kind = {"lex": oracle.ORDER_LEX, "blocked": oracle.ORDER_BLOCKED}[ordering]
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), ordering, (8, 8, 8), bed.periodic)
+    cells, _, adj = oracle.build_sparse(bed.flags, kind, (8, 8, 8), bed.periodic)
     np.testing.assert_array_equal(lat.cells().cpu().numpy(), cells)
     np.testing.assert_array_equal(lat.adjacency().cpu().numpy(), adj)
     st = LBMState(lat, "f64")
@@ -274,6 +277,6 @@ def test_large_bed_sampled_parity():
     for j, n in enumerate(sample):
         g = np.concatenate([[prev[n]], prev[adj[:, n]]])
         ref[:, j], _, _ = oracle.collide(g, F, 0.0, WP, WM)
-    fp64_measures.check(nxt[:, sample], ref, 1, label="large bed, one step, 2000 cells")
+    fp64_measures.check(nxt[:, sample], ref, 1, label=f"large bed {ordering}, one step, 2000 cells")
     st.close()
     lat.close()
