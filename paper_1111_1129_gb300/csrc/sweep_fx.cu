@@ -92,13 +92,9 @@ __device__ __forceinline__ int64_t fxmul(int64_t x, int64_t c63) { return __mul6
 // slots in warp order, then over blocks in a fixed order.
 __device__ __forceinline__ void fx_fixed_warp_sums(int64_t drho, int64_t ux, int64_t uy,
                                                    int64_t uz, int nfix, double* partials) {
-  int64_t iv[4] = {drho, ux, uy, uz};
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) iv[j] += __shfl_down_sync(0xffffffffu, iv[j], o);
-    nfix += __shfl_down_sync(0xffffffffu, nfix, o);
-  }
+  // below 2^58 units, as warp_sum_i64 needs
+  int64_t iv[4] = {warp_sum_i64(drho), warp_sum_i64(ux), warp_sum_i64(uy), warp_sum_i64(uz)};
+  nfix = (int)__reduce_add_sync(0xffffffffu, (unsigned)nfix);
   double w[4];
   w[0] = (double)nfix + (double)iv[0] * 0x1p-58;
 #pragma unroll
