@@ -391,6 +391,38 @@ def test_adjoint_matches_finite_differences():
     assert abs(np.sum(lam0 * v) - fd) < 1e-7 * abs(fd)
 
 
+@pytest.mark.parametrize("K", [2, 3])
+def test_adjoint_equals_exact_directional_derivatives(K):
+    """The dot-product test of the transposed Jacobian, to round-off.  One
+    step is a quadratic polynomial of the state and of F (u is linear in
+    the pulled values and in F; the equilibrium is quadratic in u; rho0 = 1
+    divides nothing), and J is linear in the last pulled values.  So J after
+    K = 2 steps is a polynomial of degree 2 in f0 along any direction v, and
+    in F: its central difference is the exact derivative whatever h.  After
+    K = 3 steps it has degree 4, and (4 D(h) - D(2h)) / 3 cancels the h^2
+    term of the central difference D.  <dJ/df0, v> and dJ/dF must match
+    these to round-off (a wrong sign, index or transposition in the reverse
+    step would show at O(1))."""
+    rng, flags, alpha, F, f0 = _adjoint_case()
+    J, dF, _, lam0 = oracle.adjoint(flags, 0b100, OMEGA_P, OMEGA_M, F, K, 2, alpha=alpha, f0=f0)
+
+    def exact(fun, h):
+        def central(e):
+            return (fun(e) - fun(-e)) / (2 * e)
+        return central(h) if K == 2 else (4 * central(h) - central(2 * h)) / 3
+
+    v = rng.standard_normal(f0.shape) * (flags == 0)
+    d = exact(lambda e: _J(flags, F, alpha, f0 + e * v, K), 1e-2)
+    assert abs(np.sum(lam0 * v) - d) <= 1e-12 * abs(d), (np.sum(lam0 * v), d)
+    for k in range(3):
+        def jf(e, k=k):
+            Fe = F.copy()
+            Fe[k] += e
+            return _J(flags, Fe, alpha, f0, K)
+        d = exact(jf, 1e-3)
+        assert abs(dF[k] - d) <= 1e-12 * abs(d), (k, dF[k], d)
+
+
 # ---------------------------------------------------------------------------
 # Hilbert curve (named among the numbering schemes in Sec. 3).
 
