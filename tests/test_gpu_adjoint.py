@@ -199,3 +199,65 @@ def test_fp32_adjoint_on_128cube_bed_against_fd():
     st32.close()
     st64.close()
     lat.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-11), ("f64x", 1e-10)])
+@pytest.mark.parametrize("K", [2, 3])
+def test_fp64_adjoint_equals_exact_directional_derivatives_on_the_128cube_bed(precision, tol, K):
+    """The dot-product test at full scale, on the damped 128^3 bed (1.03 M
+    cells).  One step is a quadratic polynomial of the state and of F, so J
+    after K = 2 steps is quadratic along any direction v of f0 and in F: the
+    central difference of the GPU's own forward path is the exact
+    derivative.  After K = 3 steps J is quartic, and (4 D(h) - D(2h)) / 3
+    is exact.  <dJ/df0, v> and dJ/dF of the GPU adjoint must match these to
+    round-off: tol, relative (the FP64-storage adjoint reverses in
+    double-single arithmetic, ~48 bits)."""
+    bed = inputs.bed_cube128(0)
+    alpha_dense = inputs.alpha_field(bed.dims, seed=0)
+    F = (2e-6, -1e-6, 1e-5)
+    lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "lex", (8, 8, 8), bed.periodic)
+    cells = lat.cells().cpu().numpy()
+    n = lat.n
+    alpha = torch.from_numpy(alpha_dense.reshape(-1)[cells].copy()).cuda()
+    c, w, _ = oracle.velocity_set()
+    rng = np.random.default_rng(40 + K)
+    f0 = torch.from_numpy(w[:, None] * (1.0 + 1e-3 * rng.standard_normal((19, n)))).cuda()
+    # a direction with net axial momentum, so that <dJ/df0, v> is O(1)
+    v = torch.from_numpy(w[:, None] * (np.asarray(c, np.float64)[:, 2:3]
+                                       + 0.5 * rng.standard_normal((19, n)))).cuda()
+    st = LBMState(lat, precision)
+    st.set_damping(alpha)
+
+    def J(f, Fv):
+        st.set_pdfs(f)
+        st.step(K, WP, WM, Fv)
+        return st.reduce_flux(2)[1]
+
+    def exact(fun, h):
+        def central(e):
+            return (fun(e) - fun(-e)) / (2 * e)
+        return central(h) if K == 2 else (4 * central(h) - central(2 * h)) / 3
+
+    st.set_pdfs(f0)
+    adj = Adjoint(st, K)
+    J0 = adj.forward(WP, WM, F, 2)
+    dF, _, df0 = adj.backward(want_alpha=False, want_f0=True)
+    assert abs(J0 - J(f0, F)) <= 1e-12 * abs(J0)
+    d = exact(lambda e: J(f0 + e * v, F), 2e-3)
+    dot = float((df0 * v).sum())
+    err_f0 = abs(dot - d) / abs(d)
+    dFx = []
+    for k in range(3):
+        def jf(e, k=k):
+            Fe = list(F)
+            Fe[k] += e
+            return J(f0, tuple(Fe))
+        dFx.append(exact(jf, 1e-5))
+    # dJ/dF relative to its norm: J is the mean u_z, so the x and y
+    # components are small cross terms
+    err_F = _norm_rel(dF, dFx)
+    print(f"{precision} K={K}: <dJ/df0, v> rel err {err_f0:.2e}; dJ/dF norm-rel err {err_F:.2e}")
+    assert err_f0 <= tol and err_F <= tol, (err_f0, err_F)
+    adj.close()
+    st.close()
+    lat.close()
