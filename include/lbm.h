@@ -306,7 +306,8 @@ int lbm_step_f64_noalloc(const double* f_src_dev, double* f_dst_dev, const int32
  *
  * lbm_state_create_batched: beds[n_beds] built on the same stream (they
  *   may be released afterwards; the state keeps a remapped copy of their
- *   adjacency).  PDF arrays of the state (lbm_state_get/set_pdfs) have the
+ *   adjacency, read from each bed's public adj[18*N], which this call builds
+ *   where it is not yet built, see lbm_sparse_info).  PDF arrays of the state (lbm_state_get/set_pdfs) have the
  *   padded length N_pad; see lbm_batch_layout.  Damping, moments and the
  *   adjoint are not available on a batched state.
  * lbm_step on a batched state takes force = host double[n_beds][3];
@@ -378,8 +379,11 @@ int lbm_halo_gather(const void* src_dev, const int64_t* slots_dev, int64_t count
 typedef struct lbm_adjoint lbm_adjoint;
 
 /* Buffers for K = n_steps >= 1 steps of state st (its lattice, form and
- * damping); stride = 0 picks ceil(sqrt(K)).  The state must outlive every
- * forward and backward pass; lbm_free may release the two in either order. */
+ * damping); stride = 0 picks ceil(sqrt(K)).  The adjoint's arrays are
+ * [19][N] and read the lattice's public adj[18*N], which this call builds
+ * if it is not yet built (see lbm_sparse_info).  The state must outlive
+ * every forward and backward pass; lbm_free may release the two in either
+ * order. */
 int lbm_adjoint_create(const lbm_state* st, int32_t n_steps, int32_t stride, lbm_adjoint** out);
 
 /* Forward pass from the state's current PDFs (the state is not modified):
