@@ -73,8 +73,9 @@ __device__ __forceinline__ int64_t fxmul(int64_t x, int64_t c63) { return __mul6
 // Resident blocks of 256 threads per SM the register budget is fitted to:
 // on the 1024x256x256 bed 3 (80 registers) beat 2 (120 registers) by 15%
 // and 4 (64 registers, heavy spills) by 5%.  The reducing kernel, which
-// runs once per lbm_step call, is fitted to 3 as well: 2.07 ms per launch
-// there, against 1.84 ms for a plain step.
+// runs once per lbm_step call, is fitted to 3 as well: 1.98 ms per launch
+// there (2.19 ms at 2 blocks, 128 registers, and at 4, 64 registers with
+// 168 bytes spilled), against 1.80 ms for a plain step.
 #ifndef LBM_FX_MIN_BLOCKS
 #define LBM_FX_MIN_BLOCKS 3
 #endif
