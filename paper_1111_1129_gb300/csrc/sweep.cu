@@ -2,7 +2,8 @@
 // (Sec. 1: TRT on D3Q19; Sec. 2: sparse representation with implicit bounce
 // back; Sec. 7: pull scheme, structure of arrays, nontemporal stores).
 //
-// One thread updates one fluid cell per step:
+// One thread updates one fluid cell per step (two adjacent cells in the
+// plain steps of the 16-bit forms, sweep_pair_kernel):
 //   gather   g_0 = f[n], g_i = f[adj[i-1][n]]     (pull through the list)
 //   collide  TRT with body force and Brinkman damping, written on the nine
 //            (c, -c) pairs: with s = g_a + g_b, d = g_a - g_b,
@@ -22,6 +23,11 @@
 // the rest state in FP32, FP16 or BF16 (16-bit forms scaled by 2^k).  The
 // collision on deviations is the same formula with rho replaced by
 // rho - 1, because w_q is the equilibrium of rho = 1, u = 0.
+//
+// A state's PDF rows, and the link rows its steps read, have the stride
+// sp->ld (N rounded up to 64), so that every row starts on a 128-byte
+// boundary; the links name slots r ld + m.  Host-facing copies (set/get
+// PDFs, moments) use the plain [19][N] layout.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
