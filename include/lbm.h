@@ -178,6 +178,20 @@ int lbm_state_create(const lbm_sparse* sp, int32_t precision, int32_t scale_exp,
 int lbm_state_set_pdfs(lbm_state* st, const double* f_dev);
 int lbm_state_get_pdfs(const lbm_state* st, double* f_dev);
 
+/*
+ * Exact copies of the current PDFs as stored, for checkpoints: raw[19*N]
+ * words of the storage form (8 bytes for LBM_F64 and LBM_F64X, 4 for the
+ * FP32 forms, 2 for the 16-bit forms; the shifted forms' stored
+ * deviations, scaled codes for FP16/BF16), [19][N] as above, in device or
+ * host memory owned by the caller.  FP64 f does not always carry a shifted
+ * form's deviation: (w + d) - w differs from d where d is below ~1e-9 in
+ * FP32.  lbm_state_set_raw clears the step count, as lbm_state_set_pdfs.
+ * Queued on the state's stream (a pageable host buffer makes them
+ * synchronous).  Not available on a batched state (LBM_EINVAL).
+ */
+int lbm_state_get_raw(const lbm_state* st, void* raw);
+int lbm_state_set_raw(lbm_state* st, const void* raw);
+
 /* Put the current PDFs back to rest (f_q = w_q) and clear the step count;
  * which of the two grids is current does not change. */
 int lbm_state_reset(lbm_state* st);

@@ -43,6 +43,8 @@ SIGNATURES = {
     "lbm_state_create": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
     "lbm_state_set_pdfs": (ctypes.c_int, [_vp, _vp]),
     "lbm_state_get_pdfs": (ctypes.c_int, [_vp, _vp]),
+    "lbm_state_get_raw": (ctypes.c_int, [_vp, _vp]),
+    "lbm_state_set_raw": (ctypes.c_int, [_vp, _vp]),
     "lbm_state_reset": (ctypes.c_int, [_vp]),
     "lbm_set_damping": (ctypes.c_int, [_vp, _vp]),
     "lbm_step": (ctypes.c_int, [_vp, _i32, _d, _d, _vp]),
@@ -147,6 +149,14 @@ def lbm_state_set_pdfs(state: int, f_dev: int) -> None:
 
 def lbm_state_get_pdfs(state: int, f_dev: int) -> None:
     _check(load().lbm_state_get_pdfs(state, f_dev))
+
+
+def lbm_state_get_raw(state: int, raw: int) -> None:
+    _check(load().lbm_state_get_raw(state, raw))
+
+
+def lbm_state_set_raw(state: int, raw: int) -> None:
+    _check(load().lbm_state_set_raw(state, raw))
 
 
 def lbm_state_reset(state: int) -> None:

@@ -446,6 +446,36 @@ extern "C" int lbm_state_set_pdfs(lbm_state* st, const double* f_dev) {
   return dispatch_set(st, f_dev, 0);
 }
 
+// Raw copies between the state's padded rows (stride sp->ld) and [19][N].
+static int copy_raw(const lbm_state* st, void* dst, size_t dpitch, const void* src,
+                    size_t spitch) {
+  const size_t row = (size_t)st->sp->n * storage_bytes(st->precision);
+  LBM_CUDA_TRY(cudaMemcpy2DAsync(dst, dpitch, src, spitch, row, 19, cudaMemcpyDefault,
+                                 st->sp->stream));
+  return LBM_OK;
+}
+
+extern "C" int lbm_state_get_raw(const lbm_state* st, void* raw) {
+  clear_error();
+  if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  if (st->batch) return fail(LBM_EINVAL, "raw copies are not available on a batched state");
+  if (st->sp->n == 0) return LBM_OK;
+  if (!raw) return fail(LBM_EINVAL, "raw is NULL");
+  const size_t e = storage_bytes(st->precision);
+  return copy_raw(st, raw, (size_t)st->sp->n * e, st->buf[st->cur], (size_t)st->sp->ld * e);
+}
+
+extern "C" int lbm_state_set_raw(lbm_state* st, const void* raw) {
+  clear_error();
+  if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");
+  if (st->batch) return fail(LBM_EINVAL, "raw copies are not available on a batched state");
+  st->steps = 0;
+  if (st->sp->n == 0) return LBM_OK;
+  if (!raw) return fail(LBM_EINVAL, "raw is NULL");
+  const size_t e = storage_bytes(st->precision);
+  return copy_raw(st, st->buf[st->cur], (size_t)st->sp->ld * e, raw, (size_t)st->sp->n * e);
+}
+
 extern "C" int lbm_state_reset(lbm_state* st) {
   clear_error();
   if (!valid_state(st)) return fail(LBM_EINVAL, "not a state handle");

@@ -213,6 +213,24 @@ class LBMState:
         capi.lbm_state_set_pdfs(self._handle, f.data_ptr())
         self._keep = f
 
+    def get_raw(self) -> torch.Tensor:
+        """The current PDFs as stored ([19, N] words of the storage form,
+        as an integer tensor of the storage width): exact for every form."""
+        dtype = {8: torch.int64, 4: torch.int32, 2: torch.int16}[STORAGE_BYTES[self.precision]]
+        raw = torch.empty((19, self.n), dtype=dtype, device="cuda")
+        capi.lbm_state_get_raw(self._handle, raw.data_ptr())
+        return raw
+
+    def set_raw(self, raw: torch.Tensor) -> None:
+        """Overwrite the current PDFs with words from :meth:`get_raw` of a
+        state of the same form and scale."""
+        width = STORAGE_BYTES[self.precision]
+        raw = raw.to(device="cuda").contiguous()
+        if raw.shape != (19, self.n) or raw.element_size() != width:
+            raise ValueError(f"expected ({19}, {self.n}) words of {width} bytes")
+        capi.lbm_state_set_raw(self._handle, raw.data_ptr())
+        self._keep = raw
+
     def set_damping(self, alpha) -> None:
         if alpha is None:
             capi.lbm_set_damping(self._handle, None)
@@ -232,12 +250,13 @@ class LBMState:
         capi.lbm_state_reset(self._handle)
 
     def save(self, path: str, **meta) -> None:
-        """Checkpoint: the PDFs (decoded to FP64, which every storage form
-        round-trips exactly) with the lattice's identity, to ``path``
-        (.npz).  Extra keyword values are stored alongside."""
+        """Checkpoint: the PDFs as stored (exact) and decoded to FP64, with
+        the lattice's identity, to ``path`` (.npz).  Extra keyword values
+        are stored alongside."""
         import numpy as np
         lat = self.lattice
-        np.savez(path, pdfs=self.get_pdfs().cpu().numpy(), dims=np.array(lat.dims),
+        np.savez(path, raw=self.get_raw().cpu().numpy(), pdfs=self.get_pdfs().cpu().numpy(),
+                 dims=np.array(lat.dims),
                  ordering=np.array(lat.ordering), block=np.array(lat.block),
                  periodic=np.array(lat.periodic), n=np.array(lat.n),
                  cells=lat.cells().cpu().numpy(), precision=np.array(self.precision),
@@ -246,15 +265,22 @@ class LBMState:
 
     def load(self, path: str) -> dict:
         """Restore PDFs written by :meth:`save` into this state; the lattice
-        must be the same list (same cells in the same order).  Returns the
-        stored metadata."""
+        must be the same list (same cells in the same order).  A checkpoint
+        of the same storage form and scale is restored word for word (a run
+        resumed from it continues bit for bit); another form is converted
+        from the FP64 PDFs.  Returns the stored metadata."""
         import numpy as np
         with np.load(path) as z:
             data = {k: z[k] for k in z.files}
         if int(data["n"]) != self.n or not np.array_equal(data["cells"],
                                                           self.lattice.cells().cpu().numpy()):
             raise ValueError("checkpoint was written for a different cell list")
-        self.set_pdfs(torch.from_numpy(data["pdfs"]))
+        same_scale = (self.precision not in ("f16s", "bf16s")
+                      or int(data["scale_exp"]) == self.scale_exp)
+        if "raw" in data and str(data["precision"]) == self.precision and same_scale:
+            self.set_raw(torch.from_numpy(data["raw"]))
+        else:
+            self.set_pdfs(torch.from_numpy(data["pdfs"]))
         return data
 
     def synchronize(self, timeout_s: float = 0.0) -> None:
