@@ -448,7 +448,8 @@ int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void* ctx);
 /* Description of the last failure on this thread ("" if none). */
 const char* lbm_last_error(void);
 
-/* ABI version, currently 1. */
+/* ABI version, currently 2 (2 added lbm_state_get_raw and
+ * lbm_state_set_raw to version 1; nothing was removed or changed). */
 int32_t lbm_abi_version(void);
 
 #ifdef __cplusplus

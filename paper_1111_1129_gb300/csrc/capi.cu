@@ -101,4 +101,4 @@ extern "C" int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void* 
   return LBM_OK;
 }
 
-extern "C" int32_t lbm_abi_version(void) { return 1; }
+extern "C" int32_t lbm_abi_version(void) { return 2; }

@@ -33,7 +33,7 @@ def test_every_declared_function_is_exported(lib):
 
 
 def test_abi_version(lib):
-    assert capi.lbm_abi_version() == 1
+    assert capi.lbm_abi_version() == 2
 
 
 def test_host_side_validation(lib):
