@@ -22,7 +22,9 @@
  *     (+1,0,-1),(-1,0,+1),(0,+1,+1),(0,-1,-1),(0,+1,-1),(0,-1,+1);
  *     opp(q) = q+1 for odd q, q-1 for even q > 0.  Weights 1/3, 1/18, 1/36.
  *   - sparse index n = I_c - 1 (0-based) of the paper's contiguous index.
- *   - PDFs are structure of arrays: f[q*N + n].
+ *   - PDFs are structure of arrays: f[q*N + n] at every entry point that
+ *     takes or gives them (inside a state the rows are padded to L slots,
+ *     see lbm_build_sparse).
  *   - adjacency adj[(i-1)*N + n], i = 1..18, is the flat source slot of the
  *     pull for direction i: i*N + m when the upwind cell x - c_i is the fluid
  *     cell m, else opp(i)*N + n (half-way bounce back, applied implicitly;
