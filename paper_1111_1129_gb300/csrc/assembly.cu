@@ -124,6 +124,102 @@ __global__ void __launch_bounds__(kTileThreads)
   }
 }
 
+// ---- lexicographic order: the key is the box index --------------------------
+// A tile is then kTileKeys consecutive flag bytes, and thread t takes the
+// 16 at tile + 16 t with one 16-byte load (flags 16-byte aligned; the last,
+// partial chunk of the box byte by byte).  The generic passes above walk
+// their 16 keys one by one and were bound by those dependent rounds.
+static_assert(kTileKeys == 16 * kTileThreads, "16 keys per thread");
+
+// The 16 flags of thread t's chunk (1 past the box) and how many are inside.
+__device__ __forceinline__ int lex_chunk(const uint8_t* __restrict__ flags, int64_t box,
+                                         int64_t k0, uint32_t w[4]) {
+  if (k0 + 16 <= box) {
+    const uint4 v = *reinterpret_cast<const uint4*>(flags + k0);
+    w[0] = v.x;
+    w[1] = v.y;
+    w[2] = v.z;
+    w[3] = v.w;
+    return 16;
+  }
+  const int valid = k0 < box ? (int)(box - k0) : 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) w[j] = 0x01010101u;
+  for (int b = 0; b < valid; ++b)
+    w[b >> 2] = (w[b >> 2] & ~(0xffu << (8 * (b & 3)))) | ((uint32_t)flags[k0 + b] << (8 * (b & 3)));
+  return valid;
+}
+
+// Pass 1 in lexicographic order (as tile_count_kernel).
+__global__ void __launch_bounds__(kTileThreads)
+    tile_count_lex_kernel(const uint8_t* __restrict__ flags, int64_t box, uint32_t* counts,
+                          int* bad) {
+  uint32_t w[4];
+  lex_chunk(flags, box, (int64_t)blockIdx.x * kTileKeys + 16 * (int64_t)threadIdx.x, w);
+  uint32_t mine = 0;
+  bool any_bad = false;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    any_bad |= (w[j] & 0xfefefefeu) != 0;   // a byte other than 0 or 1
+    mine += 4u - (uint32_t)__popc(w[j]);     // bytes 0/1: popc counts the solid ones
+  }
+  if (any_bad) atomicOr(bad, 1);
+  __shared__ uint32_t warp_sum[kTileThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t s = 0;
+    for (int wv = 0; wv < kTileThreads / 32; ++wv) s += warp_sum[wv];
+    counts[blockIdx.x] = s;
+  }
+}
+
+// Pass 3 in lexicographic order (as tile_scatter_kernel): each thread's
+// fluid cells take consecutive ranks after those of the threads before it
+// (a block scan of the per-thread counts); inv is written 16 ints at a time.
+__global__ void __launch_bounds__(kTileThreads)
+    tile_scatter_lex_kernel(const uint8_t* __restrict__ flags, int64_t box,
+                            const int64_t* __restrict__ offsets, int32_t* cells, int32_t* inv) {
+  __shared__ uint32_t warp_tot[kTileThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t k0 = (int64_t)blockIdx.x * kTileKeys + 16 * (int64_t)threadIdx.x;
+  uint32_t w[4];
+  const int valid = lex_chunk(flags, box, k0, w);
+  uint32_t mine = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) mine += 4u - (uint32_t)__popc(w[j]);
+  // inclusive scan within the warp, then over the warps in order
+  uint32_t incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  uint32_t before = incl - mine;
+  for (int wv = 0; wv < warp; ++wv) before += warp_tot[wv];
+  int64_t rank = offsets[blockIdx.x] + before;
+  int32_t out[16];
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    const bool fluid = ((w[b >> 2] >> (8 * (b & 3))) & 0xffu) == 0;
+    out[b] = fluid ? (int32_t)rank : -1;
+    if (fluid) {
+      cells[rank] = (int32_t)(k0 + b);
+      ++rank;
+    }
+  }
+  if (valid == 16) {
+    int4* o = reinterpret_cast<int4*>(inv + k0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[j] = make_int4(out[4 * j], out[4 * j + 1], out[4 * j + 2], out[4 * j + 3]);
+  } else {
+    for (int b = 0; b < valid; ++b) inv[k0 + b] = out[b];
+  }
+}
+
 // Pull adjacency (Sec. 2): source slot of direction i for fluid cell n, in
 // rows of ld >= n entries naming slot r ld + m (ld = n: the public layout).
 __global__ void adjacency_kernel(int32_t nx, int32_t ny, int32_t nz, uint32_t periodic,
@@ -336,8 +432,14 @@ extern "C" int lbm_build_sparse(const uint8_t* flags, const int32_t dims[3], lbm
     if (ce != cudaSuccess) return cleanup(cuda_fail(ce, "cudaMemcpyAsync(flags)"));
     flags_dev = flags_copy;
   }
-  tile_count_kernel<<<(unsigned)ntiles, kTileThreads, 0, stream>>>(ks, flags_dev, counts,
-                                                                  (int*)(scal + 1));
+  // lexicographic order with 16-byte aligned flags takes the vector passes
+  const bool lex_vec = ks.kind == LBM_ORDER_LEX && reinterpret_cast<uintptr_t>(flags_dev) % 16 == 0;
+  if (lex_vec)
+    tile_count_lex_kernel<<<(unsigned)ntiles, kTileThreads, 0, stream>>>(flags_dev, box, counts,
+                                                                        (int*)(scal + 1));
+  else
+    tile_count_kernel<<<(unsigned)ntiles, kTileThreads, 0, stream>>>(ks, flags_dev, counts,
+                                                                    (int*)(scal + 1));
   tile_scan_kernel<<<1, 1024, 0, stream>>>(counts, ntiles, offsets, scal);
   int64_t host_scal[2] = {0, 0};
   cudaError_t e = cudaGetLastError();
@@ -362,8 +464,12 @@ extern "C" int lbm_build_sparse(const uint8_t* flags, const int32_t dims[3], lbm
     cudaGetLastError();
     return cleanup(fail(LBM_ENOMEM, "device allocation failed (%lld fluid cells)", (long long)n));
   }
-  tile_scatter_kernel<<<(unsigned)ntiles, kTileThreads, 0, stream>>>(ks, flags_dev, offsets,
-                                                                    sp->cells, sp->inv);
+  if (lex_vec)
+    tile_scatter_lex_kernel<<<(unsigned)ntiles, kTileThreads, 0, stream>>>(
+        flags_dev, box, offsets, sp->cells, sp->inv);
+  else
+    tile_scatter_kernel<<<(unsigned)ntiles, kTileThreads, 0, stream>>>(ks, flags_dev, offsets,
+                                                                      sp->cells, sp->inv);
   if (n > 0) {
     const int threads = 256;
     adjacency_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, stream>>>(

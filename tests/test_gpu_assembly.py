@@ -61,6 +61,26 @@ def test_sparse_bit_exact_packed_beds(name, block, kind):
         _check_against_oracle(bed.flags, name, block, kind, bed.periodic)
 
 
+@pytest.mark.parametrize("shape", [(23, 29, 37), (2, 3, 4096), (1, 1, 17)])
+def test_lex_vector_and_generic_passes_agree(shape):
+    """Lexicographic order with 16-byte aligned flags takes the vector passes
+    (16 flags per thread); flags at an odd address take the generic key
+    walk.  Both give the oracle's representation, through full chunks,
+    whole 4096-key tiles and a ragged tail."""
+    flags = _random_flags(shape, 0.3, sum(shape))
+    cells, inv, adj = oracle.build_sparse(flags, oracle.ORDER_LEX, (1, 1, 1), 5)
+    buf = torch.zeros(flags.size + 16, dtype=torch.uint8, device="cuda")
+    for off in (0, 1):
+        view = buf[off:off + flags.size]
+        view.copy_(torch.from_numpy(flags.reshape(-1)).cuda())
+        assert (view.data_ptr() % 16 == 0) == (off == 0)
+        lat = SparseLattice(view.reshape(shape), "lex", periodic=5)
+        np.testing.assert_array_equal(lat.cells().cpu().numpy(), cells)
+        np.testing.assert_array_equal(lat.inverse().cpu().numpy(), inv)
+        np.testing.assert_array_equal(lat.adjacency().cpu().numpy(), adj)
+        lat.close()
+
+
 def test_cells_follow_key_order():
     bed = inputs.bed_small(1)
     for name, block, kind in ORDERS:
