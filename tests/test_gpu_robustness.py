@@ -73,8 +73,20 @@ def test_raw_copies_round_trip_exactly(precision):
     assert torch.equal(c.get_raw(), a.get_raw())
     with pytest.raises(ValueError):
         c.set_raw(raw[:, :-1])
+    for fn in (capi.lbm_state_get_raw, capi.lbm_state_set_raw):
+        with pytest.raises(capi.LbmError) as ei:
+            fn(c.handle, None)
+        assert ei.value.status == capi.LBM_EINVAL
     for h in (a, b, c, lat):
         h.close()
+    # an empty list: nothing to copy, no pointer needed
+    empty = SparseLattice(torch.ones((3, 4, 5), dtype=torch.uint8).cuda(), "lex")
+    st = LBMState(empty, precision, 24)
+    capi.lbm_state_get_raw(st.handle, None)
+    capi.lbm_state_set_raw(st.handle, None)
+    assert st.get_raw().shape == (19, 0)
+    st.close()
+    empty.close()
 
 
 def test_wait_with_a_time_limit_reports_timeout_and_recovers():
