@@ -6,8 +6,10 @@ rounded up to 64), so the library accepts at most 19*L < 2^31 (N <=
 and stepped in the FP64-storage form: 1024 x 512 x 215 = 112,721,920 cells
 (L = N, the last PDF slot at 2,141,716,479) and 1023 x 511 x 215 =
 112,391,895 cells (rows padded to L = 112,391,936, the last slot at
-2,135,446,783).  Every cell sees the same history, so every cell's moments
-must equal those of a single periodic cell stepped by the oracle, and the
+2,135,446,783), in the FP64-storage form and in FP16 shifted storage (whose
+first step runs the pair sweep).  Every cell sees the same history, so
+every cell's moments must be identical and equal those of a single periodic
+cell stepped by the oracle (to FP64 round-off, or to FP16 storage), and the
 mass must stay N.  Any index that wrapped past 2^31 would break that
 uniformity.  A slightly larger all-fluid box (1024 x 512 x 256, 19*N =
 2.55e9) must be refused with LBM_EOVERFLOW before any PDF or adjacency
@@ -18,7 +20,8 @@ import pytest
 import torch
 
 import oracle
-from paper_1111_1129_gb300 import LBMState, SparseLattice, build, capi, omega_minus
+from paper_1111_1129_gb300 import (LBMState, SparseLattice, build, capi, omega_minus,
+                                   shifted_scale_exp)
 
 pytestmark = pytest.mark.gpu
 
@@ -33,8 +36,12 @@ def library():
     capi.load()
 
 
+@pytest.mark.parametrize("precision", ["f64x", "f16s"])
 @pytest.mark.parametrize("dims", [(1024, 512, 215), (1023, 511, 215)])   # x, y, z
-def test_largest_list_steps_uniformly(dims):
+def test_largest_list_steps_uniformly(dims, precision):
+    """FP64 storage (the fixed-point sweep) and FP16 shifted (the pair sweep
+    for the first step, whose rest row is read as 32-bit words and whose
+    stores are paired): every cell must leave the two steps identical."""
     n_box = dims[0] * dims[1] * dims[2]
     ld = -(-n_box // 64) * 64
     assert 19 * ld < 2 ** 31 <= 19 * 1024 * 512 * 216
@@ -43,23 +50,29 @@ def test_largest_list_steps_uniformly(dims):
     lat = SparseLattice(flags, "lex", periodic=0b111)
     del flags
     assert lat.n == n_box
-    st = LBMState(lat, "f64x")
+    k = shifted_scale_exp(1e-5) if precision == "f16s" else 0
+    st = LBMState(lat, precision, k)
     st.step(2, WP, WM, F)
     mass, flux = st.reduce_flux(0)
     rho, u = st.moments()
     # one periodic cell, two steps, in the oracle
     one = np.zeros((1, 1, 1), np.uint8)
     _, obs, rho1, u1 = oracle.run(one, 0b111, WP, WM, F, 2)
-    # u ~ 1e-6 is a sum of +-f ~ 0.03: FP64 round-off of the sums is ~1e-17
-    # absolute, ~1e-11 relative, and the two sides sum in different orders
-    assert mass == float(n_box)                     # rest + force: rho = 1 exactly
-    assert abs(flux - u1[0, 0, 0, 0]) <= 1e-10 * abs(u1[0, 0, 0, 0])
+    # f64x: u ~ 1e-6 is a sum of +-f ~ 0.03, FP64 round-off of the sums is
+    # ~1e-17 absolute, ~1e-11 relative, and the two sides sum in different
+    # orders.  FP16: deviations ~1e-6 stored to 11 bits.
+    rel = 1e-10 if precision == "f64x" else 2e-3
+    if precision == "f64x":
+        assert mass == float(n_box)                 # rest + force: rho = 1 exactly
+    else:
+        assert abs(mass - n_box) <= 1e-9 * n_box
+    assert abs(flux - u1[0, 0, 0, 0]) <= rel * abs(u1[0, 0, 0, 0])
     for d in range(3):
         col = u[d]
         assert torch.equal(col, col[:1].expand_as(col)), d   # every cell identical
-        assert abs(float(col[0]) - u1[d, 0, 0, 0]) <= 1e-10 * abs(u1[d, 0, 0, 0])
+        assert abs(float(col[0]) - u1[d, 0, 0, 0]) <= rel * abs(u1[d, 0, 0, 0])
     assert torch.equal(rho, rho[:1].expand_as(rho))
-    assert abs(float(rho[0]) - rho1[0, 0, 0]) <= 1e-15
+    assert abs(float(rho[0]) - rho1[0, 0, 0]) <= (1e-15 if precision == "f64x" else 1e-9)
     del rho, u
     st.close()
     lat.close()
