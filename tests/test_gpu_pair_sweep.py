@@ -74,7 +74,7 @@ def test_pair_steps_equal_single_cell_steps(flags, precision, damped, ordering):
 
 
 @pytest.mark.parametrize("precision", ["f16s", "bf16s", "f32s"])
-def test_large_bed_pair_steps_and_one_step_parity(precision):
+def test_large_bed_steps_and_one_step_parity(precision):
     """The 1024x256x256 bed at full size in the benchmark's configuration
     (lexicographic order, the 16-bit forms at the benchmark's scale): two
     steps in one call (the pair kernel for the 16-bit forms, then the
