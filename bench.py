@@ -616,8 +616,10 @@ def run_batch_study(args):
     """256 packed beds (cube sides uniform in {24..96}, sphere radii in
     [3, 8], forces in [1e-7, 1e-5] along z), in the storage form of
     --batch-precision (FP32 shifted by default): the autotuned batched
-    launch in L2 groups, and as one group under a CUDA graph, against the
-    same beds stepped one by one; per-bed fluxes are compared bit for bit."""
+    launch in L2 groups, with resident steps (one cooperative launch per
+    group that keeps the links in shared memory), and as one group under a
+    CUDA graph, against the same beds stepped one by one; per-bed fluxes are
+    compared bit for bit."""
     import torch
 
     from paper_1111_1129_gb300 import (BatchedState, LBMState, SparseLattice, capi,
@@ -650,12 +652,16 @@ def run_batch_study(args):
         return e0.elapsed_time(e1)
 
     out = {}
-    for label, graph, group_bytes in (("batched_l2_groups", True, -1),
-                                      ("batched_graph", True, 0),
-                                      ("batched_no_graph", False, 0)):
+    resident_cells = None
+    for label, graph, group_bytes, resident in (("batched_l2_groups", True, -1, 0),
+                                                ("batched_resident", True, -1, 1),
+                                                ("batched_graph", True, 0, 0),
+                                                ("batched_no_graph", False, 0, 0)):
         bs = BatchedState(lats, prec, k)
         bs.configure(block, cpt, graph)
         n_groups = bs.groups(group_bytes)
+        if resident:
+            n_groups, resident_cells = bs.resident(1)
         bs.step(K, WP, wm, forces)          # warm-up; captures the graph
         bs.reset()                          # back to rest, same grid parity
         ms = timed(lambda: bs.step(K, WP, wm, forces))
@@ -692,14 +698,24 @@ def run_batch_study(args):
                 "peak_kind": f"measured here: L2-resident copy, 2 x {l2_buf / 1e6:.1f} MB "
                              "FP32 buffers, 50 copies per CUDA graph, best replay of 1.5 s",
                 "peak_clocks": l2_clocks, "kernel": f"batch_sweep_kernel<{prec}> (L2 groups)"}
+    # resident steps read the links once per call: 19 loads and 19 stores per
+    # update, plus 72 bytes of links per cell and call
+    bpl_res = BYTES_PER_LUP[prec] - 72 + 72 / K
+    achieved_res = bpl_res * n_fluid * K / (out["batched_resident"]["ms"] * 1e-3) / 1e9
+    roofline_res = {"bound": "l2", "achieved": achieved_res, "peak": l2_gbs, "unit": "GB/s",
+                    "frac": achieved_res / l2_gbs, "bytes_per_lup": bpl_res,
+                    "kernel": f"batch_resident_kernel<{prec}> (groups of <= "
+                              f"{resident_cells} cells)"}
     line = {"study": "batched beds", "n_beds": 256, "fluid_cells": n_fluid, "steps": K,
-            "roofline": roofline,
+            "roofline": roofline, "roofline_resident": roofline_res,
             "ordering": args.ordering, "precision": prec,
             "scale_exp": k if prec in ("f16s", "bf16s") else None,
             "tuned": {"block": block, "cells_per_thread": cpt,
                                            "candidate_ms_block_major": cand},
             **out, "speedup_vs_separate": out["batched_l2_groups"]["mflups"] /
             out["separate_loops"]["mflups"],
+            "resident_speedup_vs_l2_groups": out["batched_resident"]["mflups"] /
+            out["batched_l2_groups"]["mflups"],
             "per_bed_flux_bit_identical": f"{same}/256"}
     print(json.dumps(line), flush=True)
     return 0

@@ -358,6 +358,29 @@ int lbm_batch_config(lbm_state* st, int32_t block, int32_t cells_per_thread, int
  * are independent, and each bed takes the same steps in the same order. */
 int lbm_batch_groups(lbm_state* st, int64_t bytes, int32_t* n_groups_out);
 
+/* Resident steps (mode 1).  The non-reducing steps of each L2 group that
+ * holds at most C cells run as ONE cooperative launch: one 1024-thread block
+ * per SM, each block reading the links of its run of the group's cells once
+ * into shared memory and keeping them for all the call's steps, with a grid
+ * barrier between steps.  A step then reads only PDFs from L2, not links.
+ * C (*cells_out) is the SM count times the longest run of whole multiples
+ * of 1024 cells whose links fit one block's shared memory (3,072 cells on
+ * GB300: 466,944).  Switching the mode
+ * re-splits the groups: with resident steps a group's working set is its two
+ * PDF grids (the byte budget of lbm_batch_groups applies to those) and a
+ * group holds at most C cells.  Groups larger than C, and calls of one step,
+ * use the per-step launches of lbm_batch_config.  Resident calls are
+ * launched directly (no graph).  Results are bit-identical to the per-step
+ * launches.  mode 0: back to per-step launches.  Only for FP32 and 16-bit
+ * arithmetic (LBM_F32, LBM_F32S, LBM_F16S, LBM_BF16S): LBM_EINVAL otherwise.
+ * Each barrier wait gives up after 2 s, which co-residency should never
+ * let happen; the next lbm_step or lbm_reduce_flux on the state then
+ * returns LBM_ETIMEOUT and the PDFs are not valid.  mode -1 is a check of
+ * that limit: every wait expects one block more than the grid holds and
+ * gives up after 20 ms, so a call of two or more steps ends with
+ * LBM_ETIMEOUT reported as above.  *n_groups_out, *cells_out may be NULL. */
+int lbm_batch_resident(lbm_state* st, int32_t mode, int32_t* n_groups_out, int64_t* cells_out);
+
 /* Autotuner: times steps_per_candidate steps under each of the nine launch
  * shapes (advancing the state by 9 * (steps_per_candidate + 1) steps, whose
  * result does not depend on the shapes), keeps the fastest, and returns it

@@ -59,6 +59,7 @@ SIGNATURES = {
     "lbm_batch_layout": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "lbm_batch_config": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
     "lbm_batch_groups": (ctypes.c_int, [_vp, _i64, _vp]),
+    "lbm_batch_resident": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
     "lbm_set_allocator": (ctypes.c_int, [LBM_ALLOC_FN, LBM_FREE_FN, _vp]),
     "lbm_batch_tune": (ctypes.c_int, [_vp, _i32, _d, _d, _vp, _vp, _vp, _vp]),
     "lbm_halo_gather": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i32, _vp]),
@@ -263,6 +264,14 @@ def lbm_batch_groups(state: int, nbytes: int) -> int:
     g = ctypes.c_int32(0)
     _check(load().lbm_batch_groups(state, int(nbytes), ctypes.byref(g)))
     return g.value
+
+
+def lbm_batch_resident(state: int, mode: int):
+    """Resident steps on (1) or off (0), or the barrier time-limit check
+    (-1); returns (number of groups, resident capacity in cells)."""
+    g, c = ctypes.c_int32(0), ctypes.c_int64(0)
+    _check(load().lbm_batch_resident(state, int(mode), ctypes.byref(g), ctypes.byref(c)))
+    return g.value, c.value
 
 
 def _forces(forces):

@@ -329,6 +329,15 @@ struct Batch {
   int32_t* d_chunk_group;  // [N_pad / kBatchChunk] group of each chunk (null: one group)
   int64_t* d_group_cell0;  // [groups]
   int64_t* d_group_span;   // [groups]
+  // Resident steps (lbm_batch_resident): a group of at most res_cells cells
+  // takes all but its reducing step in one cooperative launch of one
+  // 1024-thread block per SM, each block holding its cells' links (at most
+  // res_tile cells) in shared memory; blocks meet at a grid barrier.
+  int resident;            // 0 off, 1 on, -1 barrier check (every wait runs out)
+  int64_t res_cells, res_tile;
+  uint32_t* d_sync;        // [N_pad / kBatchChunk + 1] barrier counter of each group
+  int32_t* d_sync_err;     // set by a barrier wait that ran out of time
+  int32_t* h_sync_err;     // pinned copy, read after the stream has drained
 };
 
 // Single-state step graphs: kGraphSteps non-reducing steps captured once per

@@ -399,6 +399,14 @@ class BatchedState:
         returns the number of groups.  Results do not depend on it."""
         return capi.lbm_batch_groups(self._handle, nbytes)
 
+    def resident(self, mode: int = 1):
+        """Resident steps: each group that fits takes all but its reducing
+        step in one cooperative launch that keeps the links in shared
+        memory (1), per-step launches (0), or the barrier time-limit check
+        (-1).  Returns (number of groups, resident capacity in cells).
+        Results do not depend on it."""
+        return capi.lbm_batch_resident(self._handle, mode)
+
     def tune(self, steps_per_candidate: int, omega_plus: float, omega_minus: float, forces):
         """Pick the fastest launch shape (advances the state)."""
         return capi.lbm_batch_tune(self._handle, steps_per_candidate, omega_plus, omega_minus,

@@ -1,7 +1,8 @@
 """Batched beds (one launch per step over concatenated cell lists, per-bed
 forces, CUDA graph, tuned launch shape, L2 groups of beds stepped one group
-at a time): every bed's PDFs and flux must be bit-identical to stepping that
-bed alone, whatever the launch shape and the grouping."""
+at a time, resident steps that keep the links in shared memory across a
+call's steps): every bed's PDFs and flux must be bit-identical to stepping
+that bed alone, whatever the launch shape, the grouping and the mode."""
 import numpy as np
 import pytest
 import torch
@@ -145,26 +146,140 @@ def test_tuner_picks_a_candidate_and_keeps_results():
         lat.close()
 
 
-@pytest.mark.parametrize("group_bytes", [0, -1])
-def test_full_batch_of_256_beds_sampled(group_bytes):
+@pytest.mark.parametrize("group_bytes,resident,precision",
+                         [(0, 0, "f32s"), (-1, 0, "f32s"), (-1, 1, "f32s"), (-1, 1, "f16s")])
+def test_full_batch_of_256_beds_sampled(group_bytes, resident, precision):
     """The 256-bed workload (cube sides uniform in {24..96}, radii in [3, 8],
-    forces in [1e-7, 1e-5] along z), FP32 shifted storage, 1000 steps, as one
-    graph (one group) and in the default L2 groups: per-bed flux of 8
-    sampled beds equals their separate runs."""
+    forces in [1e-7, 1e-5] along z), 1000 steps, as one graph (one group), in
+    the default L2 groups, and with resident steps in groups of up to the
+    resident capacity (runs of ~3,200 cells that cross bed boundaries):
+    per-bed flux of 8 sampled beds equals their separate runs."""
     beds, fz = inputs.batch_beds(256, 0)
     forces = [(0.0, 0.0, float(f)) for f in fz]
     lats = _lattices(beds)
-    bs = BatchedState(lats, "f32s")
+    k = 19 if precision == "f16s" else 0
+    bs = BatchedState(lats, precision, k)
     bs.configure(256, 2, True)
     n_groups = bs.groups(group_bytes)
     assert (n_groups == 1) == (group_bytes == 0)
+    if resident:
+        n_groups, cap = bs.resident(1)
+        assert n_groups > 1 and cap >= 100_000
+        assert n_groups * cap >= bs.n_padded
     bs.step(1000, WP, WM, forces)
     mass, flux = bs.reduce_flux(2)
     assert bs.n_fluid == sum(b.n_fluid for b in beds)
-    rng = np.random.default_rng(group_bytes + 1)
+    rng = np.random.default_rng(group_bytes + 1 + resident)
     for i in rng.choice(256, 8, replace=False):
-        st = LBMState(lats[i], "f32s")
+        st = LBMState(lats[i], precision, k)
         st.step(1000, WP, WM, forces[i])
+        assert st.reduce_flux(2) == (mass[i], flux[i])
+        st.close()
+    bs.close()
+    for lat in lats:
+        lat.close()
+
+
+@pytest.mark.parametrize("precision", ["f32", "f32s", "f16s", "bf16s"])
+def test_resident_steps_bit_identical_to_separate_runs(precision):
+    """Resident steps under several groupings and call lengths (1, 2, 3 and
+    37 steps; the mode switched off and on between calls) give every bed the
+    PDFs and flux of its separate run."""
+    beds, forces = _beds()
+    lats = _lattices(beds)
+    calls = [37, 1, 2, 3]
+    ref_f, ref_flux = [], []
+    for lat, F in zip(lats, forces):
+        st = LBMState(lat, precision, 20)
+        for k in calls:
+            st.step(k, WP, WM, F)
+        ref_f.append(st.get_pdfs().cpu().numpy())
+        ref_flux.append(st.reduce_flux(2) if lat.n > 0 else None)
+        st.close()
+    for group_bytes in (-1, 1, 3 << 20):
+        bs = BatchedState(lats, precision, 20)
+        bs.groups(group_bytes)
+        n_groups, cap = bs.resident(1)
+        assert cap > 0 and n_groups >= 1
+        for j, k in enumerate(calls):
+            if j == 2:
+                bs.resident(0)
+            if j == 3:
+                bs.resident(1)
+            bs.step(k, WP, WM, forces)
+        mass, flux = bs.reduce_flux(2)
+        f_all = bs.get_pdfs().cpu().numpy()
+        for i in range(len(lats)):
+            b, c = bs.begin[i], bs.count[i]
+            np.testing.assert_array_equal(f_all[:, b:b + c], ref_f[i])
+            if ref_flux[i] is not None:
+                assert (mass[i], flux[i]) == ref_flux[i]
+            else:
+                assert (mass[i], flux[i]) == (0.0, 0.0)
+        bs.close()
+    for lat in lats:
+        lat.close()
+
+
+def test_resident_group_split_and_forms():
+    """With resident steps a group's working set is its two PDF grids and a
+    group holds at most the resident capacity; FP64 arithmetic is refused."""
+    beds, _ = _beds(7, seed=5)
+    lats = _lattices(beds)
+    bs = BatchedState(lats, "f16s", 20)
+    spans = [(c + 2047) // 2048 * 2048 for c in bs.count]
+    n1, cap = bs.resident(1)
+    per_cell = 2 * 19 * 2
+    for budget in (1, 2048 * per_cell, 3 * 2048 * per_cell, 0):
+        expect, cur = 0, 0
+        for s_ in spans:
+            if s_ == 0:
+                continue
+            if cur > 0 and ((cur + s_) * per_cell > budget or cur + s_ > cap):
+                expect += 1
+                cur = 0
+            cur += s_
+        expect += 1
+        if budget == 0:
+            expect = 1
+        assert bs.groups(budget) == expect, budget
+    with pytest.raises(capi.LbmError) as ei:
+        bs.resident(2)
+    assert ei.value.status == capi.LBM_EINVAL
+    bs.close()
+    for precision in ("f64", "f64x"):
+        bs = BatchedState(lats, precision, 0)
+        with pytest.raises(capi.LbmError) as ei:
+            bs.resident(1)
+        assert ei.value.status == capi.LBM_EINVAL
+        bs.close()
+    for lat in lats:
+        lat.close()
+
+
+def test_resident_barrier_time_limit_reports_and_recovers():
+    """Check mode: every barrier wait expects one block more than the grid
+    holds, so each resident launch gives up after its 20 ms limit; the call
+    is reported as LBM_ETIMEOUT by lbm_reduce_flux, the flag clears, and the
+    state then steps correctly from a reset."""
+    beds, forces = _beds(4, seed=6)
+    lats = _lattices(beds)
+    bs = BatchedState(lats, "f32s", 0)
+    bs.groups(1)
+    bs.resident(-1)
+    bs.step(4, WP, WM, forces)
+    with pytest.raises(capi.LbmError) as ei:
+        bs.reduce_flux(2)
+    assert ei.value.status == capi.LBM_ETIMEOUT
+    bs.resident(1)
+    bs.reset()
+    bs.step(6, WP, WM, forces)
+    mass, flux = bs.reduce_flux(2)
+    for i, lat in enumerate(lats):
+        if lat.n == 0:
+            continue
+        st = LBMState(lat, "f32s", 0)
+        st.step(6, WP, WM, forces[i])
         assert st.reduce_flux(2) == (mass[i], flux[i])
         st.close()
     bs.close()
