@@ -363,9 +363,9 @@ int lbm_batch_groups(lbm_state* st, int64_t bytes, int32_t* n_groups_out);
  * per SM, each block reading the links of its run of the group's cells once
  * into shared memory and keeping them for all the call's steps, with a grid
  * barrier between steps.  A step then reads only PDFs from L2, not links.
- * C (*cells_out) is the SM count times the longest run of whole multiples
- * of 1024 cells whose links fit one block's shared memory (3,072 cells on
- * GB300: 466,944).  Switching the mode
+ * C (*cells_out) is the SM count times the longest run (a multiple of 64
+ * cells) whose links fit one block's shared memory (3,200 cells on GB300:
+ * 486,400).  Switching the mode
  * re-splits the groups: with resident steps a group's working set is its two
  * PDF grids (the byte budget of lbm_batch_groups applies to those) and a
  * group holds at most C cells.  Groups larger than C, and calls of one step,

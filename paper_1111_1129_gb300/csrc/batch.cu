@@ -27,6 +27,11 @@
 // set_pdfs convert to and from the plain [19][N_pad] layout.  Beds are
 // independent and every bed takes the same steps in the same order, so the
 // grouping changes no result.
+//
+// Resident steps (lbm_batch_resident): a group that fits one 1024-thread
+// block per SM, each keeping the links of its run of cells in shared
+// memory, takes all but its reducing step in one cooperative launch with a
+// bounded grid barrier between steps.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -174,7 +179,10 @@ __global__ void __launch_bounds__(1024)
 // Loads that may meet data written earlier in the same launch go through
 // L2 (ld.global.cg): the non-coherent path may hold stale lines.  On a
 // periodic 80x80x72 box, 1000 FP16S steps: 64,400 MFLUP/s against 56,700
-// for chained per-step launches; the barrier costs 1.4 us per step.
+// for chained per-step launches; the barrier costs 1.4 us per step.  On 256
+// packed beds, 1000 steps: FP16S 55,729 and FP32S 49,157 MFLUP/s against
+// 54,012 and 45,852 for per-step launches in L2 groups; the launch waits
+// mostly at its barriers (every step waits for the slowest block).
 constexpr int kResidentThreads = 1024;
 // Chunks of kBatchChunk cells that one block's run of cells can touch.
 constexpr int kResidentMaxChunks = 4;
@@ -668,11 +676,10 @@ int setup_resident(lbm_state* st) {
     cudaFuncAttributes fa;
     LBM_CUDA_TRY(cudaFuncGetAttributes(&fa, batch_resident_kernel<PREC>));
     const int64_t per_cell = 18 * (int64_t)sizeof(int32_t);
-    // Each thread steps the block's cells tile / 1024 at a time, and each of
-    // those rounds waits for its gathers, so a run is a whole number of
-    // rounds: 3,072 cells on GB300 (3,200 would fit, as a fourth round).
-    int64_t tile = ((int64_t)optin - (int64_t)fa.sharedSizeBytes) / per_cell;
-    tile = tile >= kResidentThreads ? tile / kResidentThreads * kResidentThreads : tile / 64 * 64;
+    // The longest run that fits (3,200 cells on GB300).  Runs of whole
+    // 1024-cell rounds (3,072) made more groups and ran 1% slower on the 256
+    // beds in both FP16S and FP32S.
+    int64_t tile = ((int64_t)optin - (int64_t)fa.sharedSizeBytes) / per_cell / 64 * 64;
     // a run must touch at most kResidentMaxChunks chunks
     tile = std::min<int64_t>(tile, (kResidentMaxChunks - 1) * kBatchChunk);
     if (tile < 64) return fail(LBM_EINVAL, "too little shared memory for resident steps");
