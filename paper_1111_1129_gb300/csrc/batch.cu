@@ -181,8 +181,9 @@ __global__ void __launch_bounds__(1024)
 // periodic 80x80x72 box, 1000 FP16S steps: 64,400 MFLUP/s against 56,700
 // for chained per-step launches; the barrier costs 1.4 us per step.  On 256
 // packed beds, 1000 steps: FP16S 55,729 and FP32S 49,157 MFLUP/s against
-// 54,012 and 45,852 for per-step launches in L2 groups; the launch waits
-// mostly at its barriers (every step waits for the slowest block).
+// 54,012 and 45,852 for per-step launches in L2 groups.  Its warps wait
+// mostly at the barriers, but two or four independent groups per launch
+// (one block of each per SM, to fill those waits) ran no faster.
 constexpr int kResidentThreads = 1024;
 // Chunks of kBatchChunk cells that one block's run of cells can touch.
 constexpr int kResidentMaxChunks = 4;
