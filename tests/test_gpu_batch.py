@@ -285,3 +285,32 @@ def test_resident_barrier_time_limit_reports_and_recovers():
     bs.close()
     for lat in lats:
         lat.close()
+
+
+def test_resident_mode_steps_a_bed_above_the_capacity_per_step():
+    """A bed larger than the resident capacity forms a group of its own and
+    keeps the per-step launches; the small beds beside it run resident.
+    Both stay bit-identical to their separate runs."""
+    big = inputs.packed_bed((128, 128, 128), 2, 126.0, 6.0, 0.45, 11)
+    beds, forces = _beds(3, seed=7)
+    beds = [beds[0], big] + beds[1:]
+    forces = [forces[0], (2e-6, 0.0, 1e-6)] + forces[1:]
+    lats = _lattices(beds)
+    bs = BatchedState(lats, "f16s", 20)
+    n_groups, cap = bs.resident(1)
+    assert lats[1].n > cap and n_groups >= 3
+    bs.step(5, WP, WM, forces)
+    mass, flux = bs.reduce_flux(2)
+    f_all = bs.get_pdfs().cpu().numpy()
+    for i, (lat, F) in enumerate(zip(lats, forces)):
+        if lat.n == 0:
+            continue
+        st = LBMState(lat, "f16s", 20)
+        st.step(5, WP, WM, F)
+        b, c = bs.begin[i], bs.count[i]
+        np.testing.assert_array_equal(f_all[:, b:b + c], st.get_pdfs().cpu().numpy())
+        assert st.reduce_flux(2) == (mass[i], flux[i])
+        st.close()
+    bs.close()
+    for lat in lats:
+        lat.close()
