@@ -47,7 +47,10 @@
  * two in either order (a garbage collector may).  All work is queued on the
  * stream given to lbm_build_sparse (a cudaStream_t passed as void*, NULL =
  * legacy default stream); functions that return host values synchronise
- * that stream.
+ * that stream.  Distinct handles may be used from different host threads at
+ * once; one handle (and a state together with the sparse representation it
+ * was built from) must not be, since some calls fill caches inside it (the
+ * public adjacency, captured CUDA graphs).
  */
 #ifndef LBM_GB300_H
 #define LBM_GB300_H
