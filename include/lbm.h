@@ -380,7 +380,8 @@ int lbm_batch_groups(lbm_state* st, int64_t bytes, int32_t* n_groups_out);
  * let happen; the next lbm_step or lbm_reduce_flux on the state then
  * returns LBM_ETIMEOUT and the PDFs are not valid.  mode -1 is a check of
  * that limit: every wait expects one block more than the grid holds and
- * gives up after 20 ms, so a call of two or more steps ends with
+ * gives up after 20 ms, so a call of three or more steps (two or more in
+ * the cooperative launch, hence a barrier) ends with
  * LBM_ETIMEOUT reported as above.  *n_groups_out, *cells_out may be NULL. */
 int lbm_batch_resident(lbm_state* st, int32_t mode, int32_t* n_groups_out, int64_t* cells_out);
 
