@@ -388,7 +388,10 @@ int lbm_batch_resident(lbm_state* st, int32_t mode, int32_t* n_groups_out, int64
 /* Autotuner: times steps_per_candidate steps under each of the nine launch
  * shapes (advancing the state by 9 * (steps_per_candidate + 1) steps, whose
  * result does not depend on the shapes), keeps the fastest, and returns it
- * (ms_out[9], if given, receives each candidate's time in ms, block-major). */
+ * (ms_out[9], if given, receives each candidate's time in ms, block-major).
+ * The shapes are those of the per-step launches: with resident steps on,
+ * they apply only to groups above the resident capacity, so tune with
+ * resident steps off. */
 int lbm_batch_tune(lbm_state* st, int32_t steps_per_candidate, double omega_plus,
                    double omega_minus, const double* forces, int32_t* block_out,
                    int32_t* cpt_out, float* ms_out);
