@@ -800,6 +800,51 @@ def run_ordering_study(args):
     return 0
 
 
+def run_seed_study(args):
+    """MFLUP/s and fraction of the copy ceiling of the storage forms on the
+    1024x256x256 bed drawn with seeds 0-4 (lexicographic order): how much the
+    rate depends on the particular packing."""
+    import torch
+
+    from paper_1111_1129_gb300 import LBMState, SparseLattice, capi, inputs, omega_minus
+
+    capi.load()
+    wm = omega_minus(WP)
+    peak, peak_kind = _peaks()
+    forms = args.study_forms.split(",")
+    rows = []
+    for seed in range(5):
+        bed = inputs.bed_large(seed)
+        lat = SparseLattice(torch.from_numpy(bed.flags).cuda(), "lex", (1, 1, 1), bed.periodic)
+        row = {"seed": seed, "fluid_cells": lat.n, "porosity": lat.n / bed.flags.size}
+        for prec in forms:
+            st = LBMState(lat, prec, _scale_exp("large"))
+            st.step(3, WP, wm, FORCE)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st.step(args.extra_steps, WP, wm, FORCE)
+            e1.record()
+            torch.cuda.synchronize()
+            rate = lat.n * args.extra_steps / (e0.elapsed_time(e1) * 1e-3) / 1e6
+            row[f"{prec}_mflups"] = rate
+            row[f"{prec}_frac"] = rate * 1e6 * BYTES_PER_LUP[prec] / 1e9 / peak
+            st.close()
+        rows.append(row)
+        lat.close()
+    summary = {}
+    for prec in forms:
+        v = [r[f"{prec}_mflups"] for r in rows]
+        summary[prec] = {"mean_mflups": statistics.mean(v), "min": min(v), "max": max(v),
+                         "spread": (max(v) - min(v)) / statistics.mean(v),
+                         "mean_frac": statistics.mean(r[f"{prec}_frac"] for r in rows)}
+    print(json.dumps({"study": "seeds", "workload": "packed bed 1024x256x256, tube D=250 along "
+                      "x, spheres r=8, seeds 0-4", "ordering": "lex",
+                      "steps_each": args.extra_steps, "peak_gbs": peak, "peak_kind": peak_kind,
+                      "rows": rows, "summary": summary}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -824,6 +869,8 @@ def main():
     ap.add_argument("--ordering-study", action="store_true",
                     help="run the numbering-scheme study instead of the benchmark")
     ap.add_argument("--study-forms", default="f64x,f32s,f16s")
+    ap.add_argument("--seed-study", action="store_true",
+                    help="the storage forms on the large bed drawn with seeds 0-4")
     ap.add_argument("--adjoint-study", action="store_true",
                     help="time the checkpointed adjoint against the forward run")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
@@ -839,6 +886,8 @@ def main():
         return run_batch_study(args)
     if args.ordering_study:
         return run_ordering_study(args)
+    if args.seed_study:
+        return run_seed_study(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
